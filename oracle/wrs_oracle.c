@@ -1,0 +1,458 @@
+/*
+ * wrs_oracle.c -- CPU oracle for alias-table construction and sampling.
+ *
+ * TEST INFRASTRUCTURE.  This is a plain, slow, deliberately unoptimised
+ * restatement of what the method computes, used only to check the CUDA
+ * library.  Only the tests, the smoke check and the CPU-baseline leg of the
+ * benchmark load it.  It shares no code, header, table or helper with the
+ * CUDA path, and the product library never links or calls it.
+ *
+ * Source: L. Huebschle-Schneider and P. Sanders, "Parallel Weighted Random
+ * Sampling" (arXiv 1903.00227).  Citations name the paper's sections and
+ * algorithms:
+ *   Sec. 2.2 "Bucket-Based Sampling"  -- alias table definition, query, Alg. 1
+ *   Sec. 4.1 "Improved Sequential Alias Table Construction" -- Alg. 2 (sweep)
+ *   Sec. 4.2 "Shared-Memory Parallel Alias Tables" -- Alg. 3 (PSA, split, pack)
+ *   Sec. 10 "Experiments", paragraph "Optimizations" -- branchless query
+ *
+ * Exact units.  Every weight is turned into an exact non-negative integer
+ * q_i (u32 weights: q_i = w_i; binary32 weights: q_i = w_i * 2^-beta with beta
+ * the smallest exponent of a set mantissa bit, so q_i is an integer), and
+ * Q = sum q_i.  Multiplying the paper's quantities by n/(2^beta) turns the
+ * bucket capacity W/n into the integer Q and the weight of item i into the
+ * integer n*q_i.  All construction arithmetic is then exact in 128 bits
+ * (Q < 2^95 and n < 2^32 give n*Q < 2^127).
+ *
+ * Table encoding (the one reading of Sec. 2.2's "biased coin" this library
+ * fixes): bucket b holds bw_b in [0, Q], the part of its own item, and an alias.
+ * With s = max(0, bitlen(Q) - 64), Qp = Q >> s and thr_b = bw_b >> s, the coin
+ * of bucket b comes up heads for a 64-bit uniform v iff floor(v*Qp / 2^64) <
+ * thr_b.  A full bucket (bw = Q) gets alias = b.
+ *
+ * Status codes: 0 ok, 1 invalid input, 2 exact range exceeded, 3 an
+ * invariant of exact arithmetic failed (never expected).
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <limits.h>
+
+typedef unsigned __int128 u128;
+
+#define WO_OK 0
+#define WO_EINVAL 1
+#define WO_EOVERFLOW 2
+#define WO_EINTERNAL 3
+
+#define WO_Q_BITS 95 /* Q must stay below 2^95 */
+
+static u128 ld128(const uint64_t *p) { return ((u128)p[1] << 64) | p[0]; }
+static void st128(uint64_t *p, u128 v) { p[0] = (uint64_t)v; p[1] = (uint64_t)(v >> 64); }
+static int bitlen128(u128 x) { int b = 0; while (x) { ++b; x >>= 1; } return b; }
+
+/* ------------------------------------------------------------------------ */
+/* Weight normalisation: q_i and Q = sum q_i (the "W := sum w_i" line that    */
+/* opens Alg. 1, 2 and 3), in exact integer units.                            */
+/* ------------------------------------------------------------------------ */
+
+/* binary32 pattern -> value m * 2^e (m < 2^24).  Sign set, NaN, Inf: invalid. */
+static int f32_decode(uint32_t bits, uint32_t *m, int *e)
+{
+    uint32_t ex = (bits >> 23) & 0xFFu, fr = bits & 0x7FFFFFu;
+    if (bits >> 31) return 1;
+    if (ex == 0xFFu) return 1;
+    if (ex == 0) { *m = fr; *e = -149; }
+    else { *m = fr | 0x800000u; *e = (int)ex - 150; }
+    return 0;
+}
+
+static int ctz32(uint32_t x) { int c = 0; while (!(x & 1u)) { x >>= 1; ++c; } return c; }
+
+/* dtype 0: uint32 weights; dtype 1: binary32 weights (passed as raw bits).
+ * Out: q (2 words per item, lo/hi), Q (2 words), beta. */
+int wo_quantize(int dtype, const uint32_t *w, uint64_t n, uint64_t *q,
+                uint64_t *Qout, int32_t *beta_out)
+{
+    u128 Q = 0;
+    uint64_t i;
+    if (n == 0 || n >= ((uint64_t)1 << 32)) return WO_EINVAL;
+    if (dtype == 0) {
+        for (i = 0; i < n; ++i) { st128(q + 2 * i, w[i]); Q += w[i]; }
+        *beta_out = 0;
+    } else if (dtype == 1) {
+        int beta = INT_MAX;
+        for (i = 0; i < n; ++i) {
+            uint32_t m; int e;
+            if (f32_decode(w[i], &m, &e)) return WO_EINVAL;
+            if (m && e + ctz32(m) < beta) beta = e + ctz32(m);
+        }
+        if (beta == INT_MAX) return WO_EINVAL; /* every weight is zero */
+        for (i = 0; i < n; ++i) {
+            uint32_t m; int e; u128 qi = 0;
+            f32_decode(w[i], &m, &e);
+            if (m) {
+                int sh = e - beta;
+                if (sh >= 0) {
+                    if (bitlen128(m) + sh > WO_Q_BITS) return WO_EOVERFLOW;
+                    qi = (u128)m << sh;
+                } else {
+                    qi = (u128)(m >> (-sh)); /* exact: m has >= -sh trailing zeros */
+                }
+            }
+            st128(q + 2 * i, qi);
+            Q += qi;
+            if (bitlen128(Q) > WO_Q_BITS) return WO_EOVERFLOW;
+        }
+        *beta_out = beta;
+    } else {
+        return WO_EINVAL;
+    }
+    if (Q == 0) return WO_EINVAL;
+    st128(Qout, Q);
+    return WO_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Alg. 2 (Sec. 4.1): the sweeping construction.                             */
+/* i runs over light items, j over heavy items, both in index order; w is     */
+/* the part of heavy item j not yet assigned.  If w exceeds the capacity, the */
+/* next light bucket is packed with j as its alias; otherwise bucket j is     */
+/* packed with the next heavy item as its alias.  Ties (w = capacity) pack    */
+/* the heavy bucket, and items with n*q = Q are light (Sec. 2.2: w <= W/n).   */
+/* ------------------------------------------------------------------------ */
+
+typedef struct { uint64_t n; const uint64_t *q; u128 Q; } wo_in;
+
+static u128 nq(const wo_in *in, uint64_t k) { return (u128)in->n * ld128(in->q + 2 * k); }
+static int is_light(const wo_in *in, uint64_t k) { return nq(in, k) <= in->Q; }
+
+static uint64_t next_light(const wo_in *in, uint64_t k)
+{
+    while (k < in->n && !is_light(in, k)) ++k;
+    return k;
+}
+
+static uint64_t next_heavy(const wo_in *in, uint64_t k)
+{
+    while (k < in->n && is_light(in, k)) ++k;
+    return k;
+}
+
+static void put(uint64_t *bw, uint32_t *al, uint64_t b, u128 v, uint64_t a)
+{
+    st128(bw + 2 * b, v);
+    al[b] = (uint32_t)a;
+}
+
+/* A bucket holding exactly the capacity needs no alias: it points to itself. */
+static void canonicalise(uint64_t n, u128 Q, const uint64_t *bw, uint32_t *al)
+{
+    uint64_t b;
+    for (b = 0; b < n; ++b)
+        if (ld128(bw + 2 * b) == Q) al[b] = (uint32_t)b;
+}
+
+int wo_sweep(uint64_t n, const uint64_t *q, const uint64_t *Qin,
+             uint64_t *bw, uint32_t *al)
+{
+    wo_in in = { n, q, ld128(Qin) };
+    uint64_t i = next_light(&in, 0), j = next_heavy(&in, 0), k;
+    u128 w;
+    if (j == n) { /* all weights equal: every bucket is its own item */
+        for (k = 0; k < n; ++k) {
+            if (nq(&in, k) != in.Q) return WO_EINTERNAL;
+            put(bw, al, k, nq(&in, k), k);
+        }
+        return WO_OK;
+    }
+    w = nq(&in, j);
+    while (j < n) {
+        if (w > in.Q) { /* pack a light bucket */
+            if (i >= n) return WO_EINTERNAL;
+            put(bw, al, i, nq(&in, i), j);
+            w = (w + nq(&in, i)) - in.Q;
+            i = next_light(&in, i + 1);
+        } else { /* pack a heavy bucket */
+            uint64_t jn = next_heavy(&in, j + 1);
+            put(bw, al, j, w, jn < n ? jn : j);
+            if (jn < n) w = (w + nq(&in, jn)) - in.Q;
+            else if (w != in.Q) return WO_EINTERNAL; /* the last heavy ends full */
+            j = jn;
+        }
+    }
+    /* lights left once the heavies are used up must be exactly full */
+    for (; i < n; i = next_light(&in, i + 1)) {
+        if (nq(&in, i) != in.Q) return WO_EINTERNAL;
+        put(bw, al, i, nq(&in, i), i);
+    }
+    canonicalise(n, in.Q, bw, al);
+    return WO_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Alg. 3 (Sec. 4.2): PSA.  Light list l and heavy list h in index order,     */
+/* inclusive prefix sums L, H of their q, p-1 splits at n'_k = ceil(n*k/p),  */
+/* then p independent packs.                                                  */
+/*                                                                            */
+/* split(n') reading: the paper asks for i + j = n' with                      */
+/*   sigma = L[i] + H[j] <= n'W/n  and  sigma + w_{h[j+1]} > n'W/n,            */
+/* which can hold for two neighbouring j.  This oracle takes the largest such */
+/* j, i.e. j* = max{ j : n*(L[n'-j] + H[j]) <= n'*Q } over the feasible range */
+/* [max(0, n'-|l|), min(n', |h|)]; that is exactly the state of Alg. 2 after */
+/* n' buckets.  The spill is the residual of heavy h[j*] (0-based) after the  */
+/* left part: r* = n*(L[i*] + H[j*] + q_{h[j*]}) - n'*Q (0 if j* = |h|).      */
+/*                                                                            */
+/* pack reading: subproblem k starts from split k-1's state (i, j, r) with    */
+/* h[j] the current heavy item and r its unassigned part, runs exactly        */
+/* n'_k - n'_{k-1} steps of the sweep rule and must end in split k's state.   */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    const wo_in *in;
+    uint64_t nl, nh;
+    uint32_t *l, *h;
+    u128 *L, *H;
+} wo_lists;
+
+static int split_pred(const wo_lists *s, uint64_t np, uint64_t j)
+{
+    u128 sigma = s->L[np - j] + s->H[j];
+    return (u128)s->in->n * sigma <= (u128)np * s->in->Q;
+}
+
+static int wo_split(const wo_lists *s, uint64_t np, uint64_t *ri, uint64_t *rj, u128 *rr)
+{
+    uint64_t lo = np > s->nl ? np - s->nl : 0;
+    uint64_t hi = np < s->nh ? np : s->nh;
+    uint64_t a, b, j, i;
+    if (lo > hi || !split_pred(s, np, lo)) return WO_EINTERNAL;
+    a = lo; b = hi; /* pred(a) holds; the answer lies in [a, b] */
+    while (a < b) {
+        uint64_t mid = a + (b - a + 1) / 2;
+        if (split_pred(s, np, mid)) a = mid; else b = mid - 1;
+    }
+    j = a; i = np - j;
+    *ri = i; *rj = j;
+    if (j < s->nh) {
+        u128 r = (u128)s->in->n * (s->L[i] + s->H[j] + ld128(s->in->q + 2 * (uint64_t)s->h[j]))
+                 - (u128)np * s->in->Q;
+        if (r == 0 || r > nq(s->in, s->h[j])) return WO_EINTERNAL;
+        *rr = r;
+    } else {
+        *rr = 0;
+    }
+    return WO_OK;
+}
+
+/* splits (optional, 4 words per k = 0..p): n'_k, i_k, j_k, r_k low word */
+int wo_psa(uint64_t n, const uint64_t *q, const uint64_t *Qin, uint64_t p,
+           uint64_t *bw, uint32_t *al, uint64_t *splits)
+{
+    wo_in in = { n, q, ld128(Qin) };
+    wo_lists s;
+    uint64_t k, x, *si = NULL, *sj = NULL, *snp = NULL;
+    u128 *sr = NULL;
+    int rc = WO_OK;
+    if (p == 0 || p > n) return WO_EINVAL;
+    memset(&s, 0, sizeof s);
+    s.in = &in;
+    s.l = malloc(n * sizeof *s.l); s.h = malloc(n * sizeof *s.h);
+    s.L = malloc((n + 1) * sizeof *s.L); s.H = malloc((n + 1) * sizeof *s.H);
+    si = malloc((p + 1) * sizeof *si); sj = malloc((p + 1) * sizeof *sj);
+    snp = malloc((p + 1) * sizeof *snp); sr = malloc((p + 1) * sizeof *sr);
+    if (!s.l || !s.h || !s.L || !s.H || !si || !sj || !snp || !sr) { rc = WO_EINVAL; goto out; }
+
+    /* the two parallel traversals of Alg. 3, plus prefix sums of their weights */
+    s.L[0] = 0; s.H[0] = 0;
+    for (x = 0; x < n; ++x) {
+        u128 qx = ld128(q + 2 * x);
+        if (is_light(&in, x)) { s.l[s.nl] = (uint32_t)x; s.L[s.nl + 1] = s.L[s.nl] + qx; ++s.nl; }
+        else                  { s.h[s.nh] = (uint32_t)x; s.H[s.nh + 1] = s.H[s.nh] + qx; ++s.nh; }
+    }
+
+    /* boundaries: k = 0 starts with the first heavy item whole; k = p is the end */
+    snp[0] = 0; si[0] = 0; sj[0] = 0; sr[0] = s.nh ? nq(&in, s.h[0]) : 0;
+    for (k = 1; k < p; ++k) {
+        snp[k] = (uint64_t)(((u128)n * k + p - 1) / p); /* ceil(n*k/p) */
+        rc = wo_split(&s, snp[k], &si[k], &sj[k], &sr[k]);
+        if (rc) goto out;
+    }
+    snp[p] = n; si[p] = s.nl; sj[p] = s.nh; sr[p] = 0;
+
+    for (k = 1; k <= p; ++k) { /* pack(k) */
+        uint64_t i = si[k - 1], j = sj[k - 1], step;
+        u128 r = sr[k - 1];
+        for (step = snp[k - 1]; step < snp[k]; ++step) {
+            if (j < s.nh && r <= in.Q) { /* heavy bucket h[j] */
+                uint64_t jn = j + 1;
+                put(bw, al, s.h[j], r, jn < s.nh ? s.h[jn] : s.h[j]);
+                if (jn < s.nh) r = (r + nq(&in, s.h[jn])) - in.Q;
+                else { if (r != in.Q) { rc = WO_EINTERNAL; goto out; } r = 0; }
+                j = jn;
+            } else { /* light bucket l[i] */
+                if (i >= s.nl) { rc = WO_EINTERNAL; goto out; }
+                put(bw, al, s.l[i], nq(&in, s.l[i]), j < s.nh ? s.h[j] : s.l[i]);
+                if (j < s.nh) r = (r + nq(&in, s.l[i])) - in.Q;
+                else if (nq(&in, s.l[i]) != in.Q) { rc = WO_EINTERNAL; goto out; }
+                ++i;
+            }
+        }
+        if (i != si[k] || j != sj[k] || (j < s.nh && r != sr[k])) { rc = WO_EINTERNAL; goto out; }
+    }
+    canonicalise(n, in.Q, bw, al);
+    if (splits)
+        for (k = 0; k <= p; ++k) {
+            splits[4 * k + 0] = snp[k]; splits[4 * k + 1] = si[k];
+            splits[4 * k + 2] = sj[k]; splits[4 * k + 3] = (uint64_t)sr[k];
+        }
+out:
+    free(s.l); free(s.h); free(s.L); free(s.H); free(si); free(sj); free(snp); free(sr);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Alg. 1 (Sec. 2.2): Vose-style construction with stacks of heavy and light */
+/* items, in exact integers.  Reading: the stacks are filled in index order, */
+/* so pop() returns the highest remaining index.  Items whose alias is still */
+/* undefined at the end are exactly full and point to themselves.            */
+/* ------------------------------------------------------------------------ */
+
+int wo_vose(uint64_t n, const uint64_t *q, const uint64_t *Qin, uint64_t *bw, uint32_t *al)
+{
+    wo_in in = { n, q, ld128(Qin) };
+    uint32_t *hs = malloc(n * sizeof *hs), *ls = malloc(n * sizeof *ls);
+    uint8_t *set = calloc(n, 1);
+    uint64_t nh = 0, nl = 0, k;
+    int rc = WO_OK;
+    if (!hs || !ls || !set) { rc = WO_EINVAL; goto out; }
+    for (k = 0; k < n; ++k) {
+        st128(bw + 2 * k, nq(&in, k));
+        if (is_light(&in, k)) ls[nl++] = (uint32_t)k; else hs[nh++] = (uint32_t)k;
+    }
+    while (nh) {
+        uint32_t j = hs[--nh];
+        while (ld128(bw + 2 * (uint64_t)j) > in.Q) {
+            uint32_t i;
+            if (!nl) { rc = WO_EINTERNAL; goto out; }
+            i = ls[--nl];
+            al[i] = j; set[i] = 1;
+            /* (b[j].w + b[i].w) - W/n, the cancellation-avoiding order */
+            st128(bw + 2 * (uint64_t)j, (ld128(bw + 2 * (uint64_t)j) + ld128(bw + 2 * (uint64_t)i)) - in.Q);
+        }
+        ls[nl++] = j;
+    }
+    for (k = 0; k < n; ++k)
+        if (!set[k]) {
+            if (ld128(bw + 2 * k) != in.Q) { rc = WO_EINTERNAL; goto out; }
+            al[k] = (uint32_t)k;
+        }
+    canonicalise(n, in.Q, bw, al);
+out:
+    free(hs); free(ls); free(set);
+    return rc;
+}
+
+/* Alg. 1 in binary64, as the paper's classic sequential baseline.  Out: the */
+/* coin probability of each bucket (b.w * n / W) and its alias.              */
+int wo_vose_f64(uint64_t n, const double *w, double *prob, uint32_t *al)
+{
+    uint32_t *hs = malloc(n * sizeof *hs), *ls = malloc(n * sizeof *ls);
+    double *bw = malloc(n * sizeof *bw);
+    uint8_t *set = calloc(n, 1);
+    double W = 0.0, cap;
+    uint64_t nh = 0, nl = 0, k;
+    int rc = WO_OK;
+    if (!hs || !ls || !bw || !set) { rc = WO_EINVAL; goto out; }
+    for (k = 0; k < n; ++k) W += w[k];
+    cap = W / (double)n;
+    for (k = 0; k < n; ++k) {
+        bw[k] = w[k];
+        if (w[k] <= cap) ls[nl++] = (uint32_t)k; else hs[nh++] = (uint32_t)k;
+    }
+    while (nh) {
+        uint32_t j = hs[--nh];
+        while (bw[j] > cap && nl) { /* rounding may exhaust the lights first */
+            uint32_t i = ls[--nl];
+            al[i] = j; set[i] = 1;
+            bw[j] = (bw[j] + bw[i]) - cap;
+        }
+        ls[nl++] = j;
+    }
+    for (k = 0; k < n; ++k) {
+        if (!set[k]) al[k] = (uint32_t)k;
+        prob[k] = bw[k] / cap;
+    }
+out:
+    free(hs); free(ls); free(bw); free(set);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Coin encoding (see the header comment): thr_b = bw_b >> s, Qp = Q >> s.   */
+/* ------------------------------------------------------------------------ */
+
+void wo_encode(uint64_t n, const uint64_t *bw, const uint64_t *Qin,
+               uint64_t *thr, uint64_t *Qp_out, uint32_t *shift_out)
+{
+    u128 Q = ld128(Qin);
+    int s = bitlen128(Q) - 64;
+    uint64_t b;
+    if (s < 0) s = 0;
+    for (b = 0; b < n; ++b) thr[b] = (uint64_t)(ld128(bw + 2 * b) >> s);
+    *Qp_out = (uint64_t)(Q >> s);
+    *shift_out = (uint32_t)s;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as   */
+/* easy as 1, 2, 3", SC 2011): ten rounds of two 32x32->64 multiplications;  */
+/* the key is bumped by the Weyl constants before every round but the first. */
+/* ------------------------------------------------------------------------ */
+
+void wo_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out)
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    int r;
+    for (r = 0; r < 10; ++r) {
+        uint64_t p0, p1;
+        uint32_t n0, n1, n2, n3;
+        if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        p0 = (uint64_t)0xD2511F53u * c0;
+        p1 = (uint64_t)0xCD9E8D57u * c2;
+        n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        n1 = (uint32_t)p1;
+        n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        n3 = (uint32_t)p0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* ------------------------------------------------------------------------ */
+/* k independent alias queries (Sec. 2.2; Sec. 5, Cor. "kWR").  Sample s     */
+/* draws 128 bits from Philox with counter (s, stream) and key seed: the low */
+/* 64 bits u pick bucket r = floor(u*n / 2^64), the high 64 bits v toss the  */
+/* coin, and the result is r on heads, its alias on tails.                   */
+/* ------------------------------------------------------------------------ */
+
+void wo_sample(uint64_t n, const uint64_t *thr, const uint32_t *al, uint64_t Qp,
+               uint64_t k, uint64_t seed, uint64_t stream, uint32_t *out)
+{
+    uint64_t s;
+    uint32_t key[2];
+    key[0] = (uint32_t)seed; key[1] = (uint32_t)(seed >> 32);
+    for (s = 0; s < k; ++s) {
+        uint32_t ctr[4], x[4];
+        uint64_t u, v, r;
+        int heads;
+        ctr[0] = (uint32_t)s; ctr[1] = (uint32_t)(s >> 32);
+        ctr[2] = (uint32_t)stream; ctr[3] = (uint32_t)(stream >> 32);
+        wo_philox4x32_10(ctr, key, x);
+        u = (uint64_t)x[0] | ((uint64_t)x[1] << 32);
+        v = (uint64_t)x[2] | ((uint64_t)x[3] << 32);
+        r = (uint64_t)(((u128)u * n) >> 64);
+        heads = (uint64_t)(((u128)v * Qp) >> 64) < thr[r];
+        out[s] = heads ? (uint32_t)r : al[r];
+    }
+}

@@ -1,0 +1,216 @@
+"""ctypes front end of the C oracle in ``wrs_oracle.c`` (test infrastructure).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` are the only callers.  Nothing here is shared
+with the CUDA library.  Every function follows a passage of L.
+Huebschle-Schneider and P. Sanders, "Parallel Weighted Random Sampling":
+
+* ``quantize``   -- W = sum w_i (first line of Alg. 1/2/3) in exact integer units
+* ``sweep``      -- Alg. 2, the sweeping construction (Sec. 4.1)
+* ``psa``        -- Alg. 3, split + pack (Sec. 4.2)
+* ``vose``       -- Alg. 1, Vose-style construction (Sec. 2.2), exact integers
+* ``vose_f64``   -- Alg. 1 in binary64, the paper's sequential baseline
+* ``encode``     -- the 64-bit coin thresholds of the table
+* ``philox``     -- Philox4x32-10 (Salmon et al., SC 2011)
+* ``sample``     -- k alias queries (Sec. 2.2, Sec. 5 Cor. "kWR")
+
+Parity is pinned for every function by the tests in ``tests/test_oracle_pins.py``
+(closed forms, invariants, brute force and hand-worked examples).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "wrs_oracle.c")
+LIB = os.path.join(HERE, "libwrs_oracle.so")
+
+OK, EINVAL, EOVERFLOW, EINTERNAL = 0, 1, 2, 3
+U32, F32 = 0, 1
+
+_lock = threading.Lock()
+_lib = None
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"oracle {where} failed with status {code}")
+        self.code = code
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc into ``oracle/libwrs_oracle.so``."""
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
+        tmp = LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-o", tmp, SRC])
+        os.replace(tmp, LIB)
+    return LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(LIB)
+            P = ctypes.c_void_p
+            U64, I32, INT = ctypes.c_uint64, ctypes.c_int32, ctypes.c_int
+            L.wo_quantize.argtypes = [INT, P, U64, P, P, P]
+            L.wo_quantize.restype = INT
+            for f in (L.wo_sweep, L.wo_vose):
+                f.argtypes = [U64, P, P, P, P]
+                f.restype = INT
+            L.wo_psa.argtypes = [U64, P, P, U64, P, P, P]
+            L.wo_psa.restype = INT
+            L.wo_vose_f64.argtypes = [U64, P, P, P]
+            L.wo_vose_f64.restype = INT
+            L.wo_encode.argtypes = [U64, P, P, P, P, P]
+            L.wo_encode.restype = None
+            L.wo_philox4x32_10.argtypes = [P, P, P]
+            L.wo_philox4x32_10.restype = None
+            L.wo_sample.argtypes = [U64, P, P, U64, U64, U64, U64, P]
+            L.wo_sample.restype = None
+            _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray) -> int:
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data
+
+
+def u128_to_int(words: np.ndarray) -> int:
+    return int(words[0]) | (int(words[1]) << 64)
+
+
+def to_words(a: np.ndarray) -> np.ndarray:
+    """Weights as raw 32-bit words (binary32 patterns are passed by bits)."""
+    a = np.ascontiguousarray(a)
+    if a.dtype == np.float32:
+        return a.view(np.uint32)
+    if a.dtype == np.uint32:
+        return a
+    raise TypeError(f"weights must be uint32 or float32, got {a.dtype}")
+
+
+def dtype_code(a: np.ndarray) -> int:
+    return F32 if a.dtype == np.float32 else U32
+
+
+class Quantized:
+    """Exact integer weights: q[i] (two uint64 words each), Q, beta."""
+
+    def __init__(self, q: np.ndarray, Qw: np.ndarray, beta: int):
+        self.q, self.Qw, self.beta = q, Qw, beta
+
+    @property
+    def n(self) -> int:
+        return self.q.shape[0]
+
+    @property
+    def Q(self) -> int:
+        return u128_to_int(self.Qw)
+
+    def q_int(self, i: int) -> int:
+        return u128_to_int(self.q[i])
+
+
+def quantize(w: np.ndarray) -> Quantized:
+    words = to_words(w)
+    n = words.shape[0]
+    q = np.zeros((max(n, 1), 2), dtype=np.uint64)
+    Qw = np.zeros(2, dtype=np.uint64)
+    beta = ctypes.c_int32(0)
+    rc = lib().wo_quantize(dtype_code(w), _ptr(words), n, _ptr(q), _ptr(Qw), ctypes.addressof(beta))
+    if rc:
+        raise OracleError(rc, "quantize")
+    return Quantized(q[:n], Qw, beta.value)
+
+
+class Table:
+    """An alias table: exact bucket masses bw (two words each), aliases, and
+    the encoded coin thresholds thr with Qp and shift."""
+
+    def __init__(self, bw: np.ndarray, alias: np.ndarray, Qw: np.ndarray):
+        self.bw, self.alias, self.Qw = bw, alias, Qw
+        n = alias.shape[0]
+        self.thr = np.zeros(n, dtype=np.uint64)
+        qp = ctypes.c_uint64(0)
+        sh = ctypes.c_uint32(0)
+        lib().wo_encode(n, _ptr(bw), _ptr(Qw), _ptr(self.thr), ctypes.addressof(qp), ctypes.addressof(sh))
+        self.Qp, self.shift = qp.value, sh.value
+
+    @property
+    def n(self) -> int:
+        return self.alias.shape[0]
+
+    def bw_int(self, b: int) -> int:
+        return u128_to_int(self.bw[b])
+
+
+def _construct(fn, qz: Quantized, *extra) -> Table:
+    n = qz.n
+    bw = np.zeros((n, 2), dtype=np.uint64)
+    al = np.zeros(n, dtype=np.uint32)
+    rc = fn(n, _ptr(qz.q), _ptr(qz.Qw), *extra, _ptr(bw), _ptr(al))
+    if rc:
+        raise OracleError(rc, fn.__name__)
+    return Table(bw, al, qz.Qw)
+
+
+def sweep(qz: Quantized) -> Table:
+    return _construct(lib().wo_sweep, qz)
+
+
+def vose(qz: Quantized) -> Table:
+    return _construct(lib().wo_vose, qz)
+
+
+def psa(qz: Quantized, p: int, return_splits: bool = False):
+    n = qz.n
+    bw = np.zeros((n, 2), dtype=np.uint64)
+    al = np.zeros(n, dtype=np.uint32)
+    splits = np.zeros((p + 1, 4), dtype=np.uint64)
+    rc = lib().wo_psa(n, _ptr(qz.q), _ptr(qz.Qw), p, _ptr(bw), _ptr(al), _ptr(splits))
+    if rc:
+        raise OracleError(rc, "psa")
+    t = Table(bw, al, qz.Qw)
+    return (t, splits) if return_splits else t
+
+
+def vose_f64(w: np.ndarray):
+    wd = np.ascontiguousarray(w, dtype=np.float64)
+    n = wd.shape[0]
+    prob = np.zeros(n, dtype=np.float64)
+    al = np.zeros(n, dtype=np.uint32)
+    rc = lib().wo_vose_f64(n, _ptr(wd), _ptr(prob), _ptr(al))
+    if rc:
+        raise OracleError(rc, "vose_f64")
+    return prob, al
+
+
+def philox(ctr, key) -> tuple:
+    c = np.array(ctr, dtype=np.uint32)
+    k = np.array(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().wo_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return tuple(int(x) for x in out)
+
+
+def sample(thr: np.ndarray, alias: np.ndarray, Qp: int, k: int, seed: int, stream: int = 0) -> np.ndarray:
+    thr = np.ascontiguousarray(thr, dtype=np.uint64)
+    alias = np.ascontiguousarray(alias, dtype=np.uint32)
+    out = np.zeros(max(k, 1), dtype=np.uint32)
+    lib().wo_sample(thr.shape[0], _ptr(thr), _ptr(alias), Qp, k, seed, stream, _ptr(out))
+    return out[:k]
+
+
+def build_table(w: np.ndarray) -> tuple:
+    """quantize + sweep: the table the CUDA build must reproduce bit for bit."""
+    qz = quantize(w)
+    return qz, sweep(qz)
