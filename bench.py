@@ -1,0 +1,407 @@
+#!/usr/bin/env python
+"""Benchmark: alias-table build and bulk sampling at n = 10^9 on GB300.
+
+One step = one pass of the whole hot path over one batch: build the alias
+table of n = 10^9 binary32 weights (exact total, light/heavy look-back scan,
+split search, sweep) and draw k = 10^9 samples from it.  Steps cycle through
+the paper's three n = 10^9 input shapes (uniform (0,1], Zipf 0.8 and Zipf 1.5,
+randomly permuted; Sec. 10 "Input Data"), generated on the device from fixed
+seeds.  Inputs (4 GB) exceed the 129 MB L2, so no flush is needed between
+steps.
+
+Printed JSON line (rank 0): ``value`` is the build throughput over all ranks
+in Gweights/s; ``sample`` gives the sampling throughput; ``e2e`` repeats the
+step through the C ABI's host-buffer entry points with the host<->device
+copies inside the timed region; ``roofline`` is the dominant kernel against
+the measured HBM copy bandwidth; ``cpu_baseline`` times the CPU oracle on a
+bounded sample of the same workload.
+
+``--impl reference`` times the CPU oracle itself (the reference arm of this
+repository) on bounded samples of the same workload.
+
+Multi-GPU: the path does not shard (one table per GPU); under torchrun every
+rank runs an independent replica and ``value`` sums their work over the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "alias build Gweights/s + sample Gsamples/s at n=1e9 (% HBM roofline); p99 ms"
+UNIT = "Gweights/s"
+DISTS = {  # name -> (generator kind, Zipf exponent, seed)
+    "uniform": ("f32_uniform", 1.0, 7),
+    "zipf0.8": ("f32_zipf", 0.8, 5),
+    "zipf1.5": ("f32_zipf", 1.5, 6),
+}
+# algorithmic bytes per unit (weights for the build kernels, samples for the query)
+ALGO_BYTES = {"stats": 4, "stats_combine": 0, "classify": 4, "tilescan": 0, "split": 0, "sweep": 16, "sample": 16}
+BUILD_BYTES_PER_WEIGHT = 24  # three 4-B weight reads + 12-B (threshold, alias) payload
+KERNEL_NAMES = {"stats": "k_stats", "stats_combine": "k_stats_combine", "classify": "k_classify",
+                "tilescan": "k_tilescan", "split": "k_split", "sweep": "k_sweep", "sample": "k_sample"}
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=6)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=10 ** 9)
+    ap.add_argument("--k", type=int, default=10 ** 9)
+    ap.add_argument("--dists", default="uniform,zipf0.8,zipf1.5")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-sample", type=int, default=20_000_000,
+                    help="weights (and samples) per distribution for the CPU-oracle baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def source_sha() -> str:
+    h = hashlib.sha256()
+    for rel in ("paper_1903_00227_gb300/csrc/wrs_kernels.cuh", "paper_1903_00227_gb300/csrc/wrs_device.cuh"):
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(stage: str, units: int):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    if d.get("source_sha") != source_sha():
+        return None
+    e = d.get("kernels", {}).get(KERNEL_NAMES[stage])
+    if not e:
+        return None
+    return float(e["dram_bytes_per_unit"]) * units
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, enabled: bool):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        self.gpu = gpu_index
+        if enabled:
+            try:
+                os.makedirs(os.path.dirname(self.path), exist_ok=True)
+                self.fh = open(self.path, "w")
+                self.proc = subprocess.Popen(
+                    ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                     "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+            except Exception:
+                self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    mx.append(float(p[2]))
+                except ValueError:
+                    continue
+                for name, v in zip(names, p[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_run(names, n_s: int, repeats: int = 1):
+    """Time the CPU oracle (quantize + Alg. 2 sweep, then n_s queries) on the
+    first n_s weights of each distribution's recipe.  Returns totals."""
+    from oracle import wrs_oracle as O
+    from paper_1903_00227_gb300 import workloads as WL
+
+    tb = ts = 0.0
+    nw = nsmp = 0
+    steps = []
+    for r in range(repeats):
+        for name in names:
+            kind, s, seed = DISTS[name]
+            w = WL.generate(kind, n_s, seed, s)
+            t0 = time.perf_counter()
+            qz = O.quantize(w)
+            tab = O.sweep(qz)
+            t1 = time.perf_counter()
+            O.sample(tab.thr, tab.alias, tab.Qp, n_s, 2, 0)
+            t2 = time.perf_counter()
+            tb += t1 - t0
+            ts += t2 - t1
+            nw += n_s
+            nsmp += n_s
+            steps.append((t2 - t0) * 1e3)
+    return tb, ts, nw, nsmp, steps
+
+
+def cpu_baseline(names, n_s: int):
+    tb, ts, nw, nsmp, _ = cpu_oracle_run(names, n_s)
+    return {"value": nw / tb / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample_gsamples_s": nsmp / ts / 1e9,
+            "sample": f"first {n_s:,} weights of each of {', '.join(names)} (same recipes), "
+                      f"exact quantize + Alg. 2 sweep, then {n_s:,} queries each; single thread"}
+
+
+def config(args, names):
+    return {"workload": f"n={args.n:.0e} binary32 weights ({', '.join(names)}; randomly permuted), "
+                        f"table build + k={args.k:.0e} samples per step, steps cycle the distributions",
+            "n": args.n, "k": args.k, "dists": names, "tile": 4096,
+            "l2": "inputs larger than L2 (4 GB weights, 16 GB table vs 129 MB L2)",
+            "parallelism": "replicas"}
+
+
+def run_reference(args, names):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    n_s = min(args.cpu_sample, args.n) // 4  # each step: one distribution, bounded sample
+    for i in range(args.warmup):
+        cpu_oracle_run([names[i % len(names)]], n_s)
+    tb = ts = 0.0
+    nw = 0
+    steps = []
+    for i in range(args.steps):
+        b, s, w_, _, st = cpu_oracle_run([names[i % len(names)]], n_s)
+        tb += b
+        ts += s
+        nw += w_
+        steps += st
+    value = nw / tb / 1e9
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": statistics.mean(steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u128", "data": "synthetic",
+            "config": config(args, names), "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"each step: first {n_s:,} weights of one distribution, "
+                                       f"quantize + sweep + {n_s:,} queries, single thread"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, names):
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import __graft_entry__ as g
+
+    if rank == 0 or ws == 1:
+        g.build()
+    if ws > 1:
+        torch.distributed.barrier()
+    from paper_1903_00227_gb300 import workloads as WL
+    from paper_1903_00227_gb300 import wrs
+
+    n, k = args.n, args.k
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    weights = {}
+    for name in names:
+        kind, s, seed = DISTS[name]
+        weights[name] = WL.generate_device(kind, n, seed, s)
+    table = wrs.AliasTable(n)
+    table.set_timing(True)
+    out = torch.empty(k, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+
+    def step(i, record):
+        name = names[i % len(names)]
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e2 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        table.build(weights[name], stream=sh)
+        e1.record(stream)
+        table.sample(k, seed=1000 + i, stream_id=0, out=out, stream=sh)
+        e2.record(stream)
+        e2.synchronize()
+        if record:
+            st = table.stage_ms()
+            return name, e0.elapsed_time(e1), e1.elapsed_time(e2), st
+        return None
+
+    for i in range(args.warmup):
+        step(i, False)
+    if table.status() != wrs.OK:
+        raise RuntimeError(f"build failed: {wrs.status_str(table.status())}")
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local, enabled=(rank == 0 and not args.no_clocks))
+    time.sleep(0.3)
+    recs = [step(args.warmup + i, True) for i in range(args.steps)]
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if ws > 1:
+        torch.distributed.barrier()
+    status = table.status()
+    if status != wrs.OK:
+        raise RuntimeError(f"build failed in the timed region: {wrs.status_str(status)}")
+
+    t_build = sum(r[1] for r in recs)
+    t_sample = sum(r[2] for r in recs)
+    step_ms = [r[1] + r[2] for r in recs]
+    if ws > 1:
+        tt = torch.tensor([t_build, t_sample, sum(step_ms)], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_build, t_sample, _ = tt.tolist()
+    K = args.steps
+    value = ws * K * n / (t_build * 1e-3) / 1e9
+    sample_rate = ws * K * k / (t_sample * 1e-3) / 1e9
+
+    # per-kernel mean durations (events on the launching stream)
+    stage_ms = {s: statistics.mean(r[3][s] for r in recs) for s in wrs.STAGES}
+    stage_ms["sample"] = statistics.mean(r[2] for r in recs)
+    peak, peak_kind = measured_peaks()
+    units = {s: n for s in wrs.STAGES}
+    units["sample"] = k
+    dom = max(stage_ms, key=stage_ms.get)
+    achieved = ALGO_BYTES[dom] * units[dom] / (stage_ms[dom] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": KERNEL_NAMES[dom], "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": traffic_for(dom, units[dom]),
+                "peak_source": peak_kind, "algorithmic_bytes_per_unit": ALGO_BYTES[dom]}
+    build_mean = t_build / K
+    ach_build = BUILD_BYTES_PER_WEIGHT * n / (build_mean * 1e-3) / 1e9
+    per_kernel = {KERNEL_NAMES[s]: {"ms": stage_ms[s],
+                                    "gbs": (ALGO_BYTES[s] * units[s] / (stage_ms[s] * 1e-3) / 1e9)
+                                    if ALGO_BYTES[s] else None} for s in stage_ms}
+    per_dist = {}
+    for name in names:
+        rs = [r for r in recs if r[0] == name]
+        if rs:
+            bm = statistics.mean(r[1] for r in rs)
+            sm_ = statistics.mean(r[2] for r in rs)
+            per_dist[name] = {"build_ms": bm, "build_gweights_s": n / (bm * 1e-3) / 1e9,
+                              "build_frac": BUILD_BYTES_PER_WEIGHT * n / (bm * 1e-3) / 1e9 / peak,
+                              "sample_ms": sm_, "sample_gsamples_s": k / (sm_ * 1e-3) / 1e9}
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    e2e = None
+    if args.e2e_steps > 0:
+        h_w = torch.empty(n, dtype=torch.float32, pin_memory=True)
+        h_out = torch.empty(k, dtype=torch.int32, pin_memory=True)
+        times = []
+        for i in range(args.e2e_steps + 1):
+            name = names[i % len(names)]
+            h_w.copy_(weights[name])
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rc = wrs.table_build_host(table.handle, h_w.data_ptr(), n, wrs.F32, sh)
+            assert rc == wrs.OK, wrs.status_str(rc)
+            rc = wrs.sample_host(table.handle, k, 5000 + i, 0, h_out.data_ptr(), sh)
+            assert rc == wrs.OK, wrs.status_str(rc)
+            e1.record(stream)
+            e1.synchronize()
+            if i > 0:  # first call allocates the staging buffers
+                times.append(e0.elapsed_time(e1))
+        t_e2e = statistics.mean(times)
+        if ws > 1:
+            tt = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            t_e2e = tt.item()
+        e2e = {"value": ws * n / (t_e2e * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": 4 * n,
+               "d2h_bytes_per_step": 4 * k, "ms_per_step": t_e2e,
+               "note": "wrs_table_build_host (H2D of the weights) + wrs_sample_host (D2H of the samples)"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(names, min(args.cpu_sample, n))
+
+    if rank == 0:
+        srt = sorted(step_ms)
+        p99 = srt[min(len(srt) - 1, int(round(0.99 * (len(srt) - 1))))]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": args.warmup,
+            "ms_per_step": statistics.mean(step_ms), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u128", "data": "synthetic", "config": config(args, names),
+            "sample": {"value": sample_rate, "unit": "Gsamples/s", "ms": t_sample / K},
+            "p99_ms": p99,
+            "roofline": roofline,
+            "roofline_build": {"bound": "hbm", "achieved": ach_build, "peak": peak, "unit": "GB/s",
+                               "frac": ach_build / peak, "algorithmic_bytes_per_weight": BUILD_BYTES_PER_WEIGHT,
+                               "peak_source": peak_kind},
+            "kernels": per_kernel, "per_dist": per_dist,
+            "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
+            "gpu_launches": K * (len(wrs.STAGES) + 1),
+            "context": {"paper_psa_build_gweights_s_n1e9": 0.99, "paper_psa_query_gsamples_s_n1e9": 1.662,
+                        "paper_hardware": "4x Xeon Gold 6138, 158 threads (context only)"},
+        }
+        print(json.dumps(line), flush=True)
+    table.free()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    names = [d for d in args.dists.split(",") if d]
+    for d in names:
+        if d not in DISTS:
+            raise SystemExit(f"unknown distribution {d}")
+    if args.impl == "reference":
+        return run_reference(args, names)
+    return run_ours(args, names)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,185 @@
+/*
+ * wrs.h -- C ABI of libwrs: Walker alias tables built on a GB300 GPU with the
+ * parallel split construction, and bulk weighted sampling with replacement.
+ *
+ * The operations follow L. Huebschle-Schneider and P. Sanders, "Parallel
+ * Weighted Random Sampling":
+ *   - problem WRS-1 / WRS-R (Sec. 1): draw items X with P[X = i] = w_i / W,
+ *     k times independently;
+ *   - the alias table (Sec. 2.2): n buckets of capacity W/n, bucket i holds
+ *     part w'_i of item i and at most one other item, its alias a_i;
+ *   - its construction (Alg. 2, Sec. 4.1; Alg. 3 "PSA", Sec. 4.2) and its
+ *     query: a uniform bucket r and a biased coin, heads -> r, tails -> a_r
+ *     (Sec. 2.2; k queries: Sec. 5, Cor. "kWR").
+ *
+ * Conventions for every entry point:
+ *   - Pointers named d_* are CUDA device pointers, h_* are host pointers.
+ *     No torch or CUDA types appear here: a stream is a cudaStream_t passed
+ *     as void* (NULL = the legacy default stream).
+ *   - Work is enqueued on the given stream and the call returns without
+ *     waiting, unless its comment says it synchronises.
+ *   - Argument errors are returned at once and enqueue nothing.  Errors the
+ *     GPU detects (invalid weights, exact range exceeded, a bounded wait that
+ *     ran out, a broken invariant) are stored in the table's device status
+ *     word; wrs_table_status() reads it.  A sample call on a table whose
+ *     build failed writes nothing.
+ *   - Determinism: the table is a pure function of the weights, and sample s
+ *     of a call is a pure function of (table, seed, stream_id, s); neither
+ *     depends on the launch configuration.
+ */
+#ifndef WRS_H
+#define WRS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    WRS_OK = 0,
+    WRS_EINVAL = 1,     /* bad argument or invalid weights (NaN, Inf, sign bit set, all zero) */
+    WRS_ENOMEM = 2,     /* a device or pinned-host allocation failed */
+    WRS_EOVERFLOW = 3,  /* the weights' exact sum needs more than 95 bits */
+    WRS_ETIMEOUT = 4,   /* a bounded wait between thread blocks gave up */
+    WRS_EDEVICE = 5,    /* a CUDA runtime call failed */
+    WRS_EINTERNAL = 6   /* an invariant of exact arithmetic failed (never expected) */
+} wrs_status;
+
+typedef enum {
+    WRS_U32 = 0,        /* uint32 weights: item i has exact weight q_i = w_i */
+    WRS_F32 = 1         /* IEEE binary32 weights >= +0, finite; exact, see below */
+} wrs_dtype;
+
+/*
+ * One bucket of the table, 16 bytes, array of structures (Sec. 10 "Sequential
+ * Performance": one cache access per query).  With Q the exact weight total
+ * in integer units (below), shift = max(0, bitlen(Q) - 64) and qp = Q >> shift,
+ * the coin of bucket r comes up heads for a 64-bit uniform v iff
+ * floor(v * qp / 2^64) < thr.  thr = bw >> shift, where bw in [0, Q] is the
+ * part of item r that the bucket holds, in units where every bucket holds Q
+ * and item i weighs n * q_i.  A full bucket points to itself.
+ */
+typedef struct {
+    uint64_t thr;
+    uint32_t alias;
+    uint32_t reserved; /* zero */
+} wrs_bucket;
+
+/*
+ * Exact integer units: u32 weights are used as they are (q_i = w_i, beta = 0).
+ * For binary32 weights, beta is the smallest exponent of a set bit over all
+ * nonzero weights and q_i = w_i * 2^-beta, an exact integer.  Q = sum q_i
+ * must stay below 2^95, else the build fails with WRS_EOVERFLOW.
+ */
+typedef struct {
+    uint64_t n;          /* number of items / buckets */
+    uint64_t q_lo, q_hi; /* Q, the exact weight total in integer units */
+    int32_t beta;        /* exponent of the integer unit (binary32 weights) */
+    uint32_t shift;      /* thr = bw >> shift */
+    uint64_t qp;         /* Q >> shift, the coin denominator */
+    uint64_t n_light;    /* items with n * q_i <= Q (Sec. 2.2: light) */
+    uint32_t light_max;  /* an item is light iff its raw 32-bit word <= light_max */
+    int32_t status;      /* wrs_status of the last build */
+} wrs_table_info;
+
+typedef struct wrs_table wrs_table; /* opaque; device memory owned by the library */
+
+/* Allocate a table (buckets and workspace) for up to capacity_n weights.
+ * capacity_n in [1, 2^32 - 1].  Synchronous (cudaMalloc); the table can be
+ * rebuilt any number of times.  Device memory: 16 B per bucket plus about
+ * 0.09 B per weight of workspace.  Errors: WRS_EINVAL, WRS_ENOMEM. */
+wrs_status wrs_table_create(uint64_t capacity_n, wrs_table **out);
+
+/* Build the alias table of n weights (Alg. 3 "PSA", Sec. 4.2, with the exact
+ * split of Alg. 2's state; identical bucket for bucket to Alg. 2).  d_weights:
+ * n words of dtype, device memory, 4-byte aligned, read only; the caller may
+ * free or overwrite it once the build has completed on `stream`.  n in [1,
+ * capacity].  Allocates nothing; asynchronous.  Device-detected errors go to
+ * the table's status word.  Errors returned at once: WRS_EINVAL. */
+wrs_status wrs_table_build(wrs_table *t, const void *d_weights, uint64_t n,
+                           wrs_dtype dtype, void *stream);
+
+/* wrs_table_create(n) followed by wrs_table_build(). */
+wrs_status wrs_build(const void *d_weights, uint64_t n, wrs_dtype dtype,
+                     void *stream, wrs_table **out);
+
+/* Draw k samples with replacement (Sec. 2.2 query, k times; Sec. 5 Cor.
+ * "kWR"): for s in [0, k), Philox4x32-10 with counter (s, stream_id) and key
+ * seed gives 128 bits; the low 64 bits u pick bucket r = floor(u * n / 2^64),
+ * the high 64 bits toss r's coin; d_out[s] = heads ? r : alias_r.  d_out:
+ * caller-owned device memory for k uint32.  k may be 0.  Asynchronous,
+ * ordered after the last build on the stream the caller chose.  Does not
+ * synchronise: if the last build failed on the device, the kernel writes
+ * nothing and wrs_table_status() reports why.  Errors returned at once:
+ * WRS_EINVAL (bad argument, table never built), or a failed build's status
+ * if wrs_table_status()/wrs_table_info_get() already read it. */
+wrs_status wrs_sample(const wrs_table *t, uint64_t k, uint64_t seed,
+                      uint64_t stream_id, uint32_t *d_out, void *stream);
+
+/* End-to-end variants with HOST buffers: copy h_weights (n words) to the
+ * table's device staging buffer, build, and return after enqueueing; and
+ * sample into device staging memory and copy the k results to h_out.  The
+ * copies are stream-ordered cudaMemcpyAsync calls; pinned host memory makes
+ * them asynchronous.  wrs_sample_host synchronises `stream` before it
+ * returns, so h_out is ready.  Staging memory is allocated on first use and
+ * kept by the table (so the first call allocates; later calls of equal or
+ * smaller size do not). */
+wrs_status wrs_table_build_host(wrs_table *t, const void *h_weights, uint64_t n,
+                                wrs_dtype dtype, void *stream);
+wrs_status wrs_sample_host(wrs_table *t, uint64_t k, uint64_t seed,
+                           uint64_t stream_id, uint32_t *h_out, void *stream);
+
+/* Synchronise the device and return the status word of the last build. */
+wrs_status wrs_table_status(const wrs_table *t);
+
+/* Synchronise and fill *info (header of the last build). */
+wrs_status wrs_table_info_get(const wrs_table *t, wrs_table_info *info);
+
+/* Device pointer to the n buckets (wrs_bucket[n]) of the last build; owned
+ * by the table, valid until the table is freed or rebuilt. */
+const wrs_bucket *wrs_table_buckets(const wrs_table *t);
+
+/* Synchronise and copy n buckets to h_buckets (bytes >= 16 n). */
+wrs_status wrs_table_download(const wrs_table *t, void *h_buckets, uint64_t bytes);
+
+/* Install buckets computed elsewhere (for testing the query on its own):
+ * copies n buckets from host memory and sets Q, beta; shift and qp are
+ * derived from Q as in a build.  Synchronous. */
+wrs_status wrs_table_upload(wrs_table *t, const void *h_buckets, uint64_t n,
+                            uint64_t q_lo, uint64_t q_hi, int32_t beta);
+
+/* Stage timing: when enabled, every later build records CUDA events on its
+ * stream between its six kernels (weight total, total combine, tile
+ * classification, look-back scan of the tile sums, split search, sweep).
+ * wrs_table_stage_ms waits for the last build and writes the first `count`
+ * (<= 6) stage durations in milliseconds.
+ * Enabling creates the events (no device memory); errors: WRS_EINVAL when
+ * timing is off or no timed build exists. */
+wrs_status wrs_table_set_timing(wrs_table *t, int enable);
+wrs_status wrs_table_stage_ms(const wrs_table *t, float *ms, uint32_t count);
+
+/* Free all memory of the table (synchronises the device first).  NULL ok. */
+void wrs_table_free(wrs_table *t);
+
+/* Static string for a status code. */
+const char *wrs_status_str(wrs_status s);
+
+/* Device-side wait limit used by the look-back scan of a build, in polls
+ * (default 1 << 22, about a second).  Returns the previous value.  A build
+ * whose wait runs out stores WRS_ETIMEOUT in the table's status. */
+uint32_t wrs_set_wait_limit(uint32_t polls);
+
+/* Test hook: during the next build, block `tile` of the look-back scan (it
+ * covers 256 tiles of 2048 weights) publishes nothing, so its successor's
+ * bounded wait runs out and the build ends with WRS_ETIMEOUT instead of
+ * waiting forever.  -1 (the default) disables it.  For failure-detection
+ * tests only. */
+void wrs_debug_skip_publish(int64_t tile);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WRS_H */

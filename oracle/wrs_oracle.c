@@ -456,3 +456,25 @@ void wo_sample(uint64_t n, const uint64_t *thr, const uint32_t *al, uint64_t Qp,
         out[s] = heads ? (uint32_t)r : al[r];
     }
 }
+
+/* The same queries for an explicit list of sample indices s_idx[0..m). */
+void wo_sample_at(uint64_t n, const uint64_t *thr, const uint32_t *al, uint64_t Qp,
+                  uint64_t seed, uint64_t stream, const uint64_t *s_idx, uint64_t m, uint32_t *out)
+{
+    uint64_t t;
+    for (t = 0; t < m; ++t) {
+        uint32_t one;
+        uint64_t s = s_idx[t];
+        uint32_t key[2], ctr[4], x[4];
+        uint64_t u, v, r;
+        key[0] = (uint32_t)seed; key[1] = (uint32_t)(seed >> 32);
+        ctr[0] = (uint32_t)s; ctr[1] = (uint32_t)(s >> 32);
+        ctr[2] = (uint32_t)stream; ctr[3] = (uint32_t)(stream >> 32);
+        wo_philox4x32_10(ctr, key, x);
+        u = (uint64_t)x[0] | ((uint64_t)x[1] << 32);
+        v = (uint64_t)x[2] | ((uint64_t)x[3] << 32);
+        r = (uint64_t)(((u128)u * n) >> 64);
+        one = ((uint64_t)(((u128)v * Qp) >> 64) < thr[r]) ? (uint32_t)r : al[r];
+        out[t] = one;
+    }
+}

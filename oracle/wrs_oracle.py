@@ -75,6 +75,8 @@ def lib():
             L.wo_philox4x32_10.restype = None
             L.wo_sample.argtypes = [U64, P, P, U64, U64, U64, U64, P]
             L.wo_sample.restype = None
+            L.wo_sample_at.argtypes = [U64, P, P, U64, U64, U64, P, U64, P]
+            L.wo_sample_at.restype = None
             _lib = L
     return _lib
 
@@ -214,3 +216,13 @@ def build_table(w: np.ndarray) -> tuple:
     """quantize + sweep: the table the CUDA build must reproduce bit for bit."""
     qz = quantize(w)
     return qz, sweep(qz)
+
+
+def sample_at(thr: np.ndarray, alias: np.ndarray, Qp: int, seed: int, stream: int, idx: np.ndarray) -> np.ndarray:
+    """The queries of ``sample`` for the sample indices ``idx`` only."""
+    thr = np.ascontiguousarray(thr, dtype=np.uint64)
+    alias = np.ascontiguousarray(alias, dtype=np.uint32)
+    idx = np.ascontiguousarray(idx, dtype=np.uint64)
+    out = np.zeros(max(idx.shape[0], 1), dtype=np.uint32)
+    lib().wo_sample_at(thr.shape[0], _ptr(thr), _ptr(alias), Qp, seed, stream, _ptr(idx), idx.shape[0], _ptr(out))
+    return out[: idx.shape[0]]

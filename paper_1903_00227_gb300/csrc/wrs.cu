@@ -1,0 +1,399 @@
+// wrs.cu -- libwrs: the C ABI declared in include/wrs.h and the table
+// runtime around the kernels of wrs_kernels.cuh (workspace layout, launch
+// configuration, stream ordering, status handling).
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <cstring>
+#include <new>
+
+#include "wrs.h"
+#include "wrs_kernels.cuh"
+
+using namespace wrs;
+
+constexpr int kStages = 6; // stats, stats_combine, classify, tilescan, split, sweep
+
+struct wrs_table {
+    uint64_t cap;          // capacity in weights
+    uint64_t n;            // weights of the last build (0: never built)
+    uint32_t ntiles_cap;
+    uint32_t epoch;        // look-back flag generation
+    int device;
+    uint8_t *ws;           // workspace block
+    DevHeader *hdr;
+    Partial *part;
+    TileSum *agg, *incl;        // per tile
+    TileSum *cagg, *cincl;      // per look-back chunk (256 tiles)
+    uint32_t *flags;            // per chunk
+    Split *split;
+    uint16_t *slist;            // per tile, kSparse offsets
+    uint4 *buckets;        // wrs_bucket[cap]
+    void *stage_w;         // host-API staging (weights), bytes = stage_w_bytes
+    uint64_t stage_w_bytes;
+    uint32_t *stage_out;   // host-API staging (samples)
+    uint64_t stage_out_cap;
+    int host_status;       // last status read back (-1: unknown)
+    cudaEvent_t ev[kStages + 1]; // stage timing (created when enabled)
+    int timing;            // record ev[] around the build's kernels
+    int timed_build;       // the last build recorded ev[]
+};
+
+namespace {
+
+constexpr uint32_t kMaxParts = 2048;     // blocks of k_stats
+std::atomic<uint32_t> g_wait_limit{1u << 22};
+std::atomic<int64_t> g_skip_tile{-1};
+
+inline uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
+
+struct Layout {
+    uint64_t hdr, part, agg, incl, cagg, cincl, flags, split, slist, total;
+};
+
+Layout layout_for(uint32_t ntiles)
+{
+    const uint32_t nchunks = (ntiles + kScanChunk - 1) / kScanChunk;
+    Layout L;
+    uint64_t o = 0;
+    L.hdr = o; o = align_up(o + sizeof(DevHeader), 256);
+    L.part = o; o = align_up(o + kMaxParts * sizeof(Partial), 256);
+    L.agg = o; o = align_up(o + (uint64_t)ntiles * sizeof(TileSum), 256);
+    L.incl = o; o = align_up(o + (uint64_t)ntiles * sizeof(TileSum), 256);
+    L.cagg = o; o = align_up(o + (uint64_t)nchunks * sizeof(TileSum), 256);
+    L.cincl = o; o = align_up(o + (uint64_t)nchunks * sizeof(TileSum), 256);
+    L.flags = o; o = align_up(o + (uint64_t)nchunks * sizeof(uint32_t), 256);
+    L.split = o; o = align_up(o + (uint64_t)ntiles * sizeof(Split), 256);
+    L.slist = o; o = align_up(o + (uint64_t)ntiles * kSparse * sizeof(uint16_t), 256);
+    L.total = o;
+    return L;
+}
+
+inline wrs_status cuda_err(cudaError_t e)
+{
+    if (e == cudaSuccess) return WRS_OK;
+    if (e == cudaErrorMemoryAllocation) return WRS_ENOMEM;
+    return WRS_EDEVICE;
+}
+
+inline wrs_status launch_err() { return cuda_err(cudaGetLastError()); }
+
+int sm_count()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+wrs_status enqueue_build(wrs_table *t, const void *d_weights, uint64_t n, wrs_dtype dtype, cudaStream_t s)
+{
+    const uint32_t *w = static_cast<const uint32_t *>(d_weights);
+    const int vec = (reinterpret_cast<uintptr_t>(w) % 16) == 0;
+    const uint32_t ntiles = (uint32_t)((n + kTile - 1) / kTile);
+    const uint32_t f32 = dtype == WRS_F32;
+    uint64_t want = (n + (uint64_t)kThreads * 16 - 1) / ((uint64_t)kThreads * 16);
+    uint32_t nparts = (uint32_t)(want < 1 ? 1 : (want > kMaxParts ? kMaxParts : want));
+    uint32_t blocks_cap = (uint32_t)sm_count() * 8;
+    if (nparts > blocks_cap) nparts = blocks_cap;
+
+    t->epoch = t->epoch + 1;
+    if (t->epoch >= (1u << 30)) t->epoch = 1;
+    const uint32_t epoch = t->epoch;
+    const uint32_t wait_limit = g_wait_limit.load();
+    const int64_t skip = g_skip_tile.exchange(-1);
+    const uint32_t skip_tile = skip < 0 ? kNone : (uint32_t)skip;
+
+    const uint32_t nchunks = (ntiles + kScanChunk - 1) / kScanChunk;
+    uint32_t cls_blocks = (uint32_t)sm_count() * 8;
+    if (cls_blocks > ntiles) cls_blocks = ntiles;
+    const bool tm = t->timing != 0;
+    if (tm) cudaEventRecord(t->ev[0], s);
+    if (f32) k_stats<1><<<nparts, kThreads, 0, s>>>(w, n, vec, t->part);
+    else k_stats<0><<<nparts, kThreads, 0, s>>>(w, n, vec, t->part);
+    if (tm) cudaEventRecord(t->ev[1], s);
+    k_stats_combine<<<1, kThreads, 0, s>>>(t->part, nparts, n, f32, t->hdr);
+    if (tm) cudaEventRecord(t->ev[2], s);
+    if (f32) k_classify<1><<<cls_blocks, kThreads, 0, s>>>(w, n, vec, t->hdr, t->agg, t->slist, ntiles);
+    else k_classify<0><<<cls_blocks, kThreads, 0, s>>>(w, n, vec, t->hdr, t->agg, t->slist, ntiles);
+    if (tm) cudaEventRecord(t->ev[3], s);
+    k_tilescan<<<nchunks, kThreads, 0, s>>>(t->hdr, t->agg, t->cagg, t->cincl, t->incl, t->flags, ntiles, epoch,
+                                            wait_limit, skip_tile);
+    if (tm) cudaEventRecord(t->ev[4], s);
+    k_split<<<(ntiles + kThreads - 1) / kThreads, kThreads, 0, s>>>(t->incl, ntiles, n, t->hdr, t->split);
+    if (tm) cudaEventRecord(t->ev[5], s);
+    if (f32) k_sweep<1><<<ntiles, kThreads, 0, s>>>(w, n, vec, t->hdr, t->incl, t->split, t->slist, ntiles, t->buckets);
+    else k_sweep<0><<<ntiles, kThreads, 0, s>>>(w, n, vec, t->hdr, t->incl, t->split, t->slist, ntiles, t->buckets);
+    if (tm) cudaEventRecord(t->ev[6], s);
+    t->timed_build = tm;
+    wrs_status st = launch_err();
+    if (st == WRS_OK) {
+        t->n = n;
+        t->host_status = -1;
+    }
+    return st;
+}
+
+wrs_status read_status(const wrs_table *t, uint32_t *out)
+{
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return WRS_EDEVICE;
+    e = cudaMemcpy(out, &t->hdr->status, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+    return cuda_err(e);
+}
+
+} // namespace
+
+extern "C" {
+
+wrs_status wrs_table_create(uint64_t capacity_n, wrs_table **out)
+{
+    if (!out) return WRS_EINVAL;
+    *out = nullptr;
+    if (capacity_n == 0 || capacity_n >= (1ull << 32)) return WRS_EINVAL;
+    wrs_table *t = new (std::nothrow) wrs_table();
+    if (!t) return WRS_ENOMEM;
+    std::memset(t, 0, sizeof(*t));
+    t->cap = capacity_n;
+    t->ntiles_cap = (uint32_t)((capacity_n + kTile - 1) / kTile);
+    t->host_status = -1;
+    cudaGetDevice(&t->device);
+    const Layout L = layout_for(t->ntiles_cap);
+    cudaError_t e = cudaMalloc(&t->ws, L.total);
+    if (e != cudaSuccess) { delete t; return cuda_err(e); }
+    e = cudaMalloc(&t->buckets, capacity_n * sizeof(uint4));
+    if (e != cudaSuccess) { cudaFree(t->ws); delete t; return cuda_err(e); }
+    t->hdr = reinterpret_cast<DevHeader *>(t->ws + L.hdr);
+    t->part = reinterpret_cast<Partial *>(t->ws + L.part);
+    t->agg = reinterpret_cast<TileSum *>(t->ws + L.agg);
+    t->incl = reinterpret_cast<TileSum *>(t->ws + L.incl);
+    t->cagg = reinterpret_cast<TileSum *>(t->ws + L.cagg);
+    t->cincl = reinterpret_cast<TileSum *>(t->ws + L.cincl);
+    t->flags = reinterpret_cast<uint32_t *>(t->ws + L.flags);
+    t->split = reinterpret_cast<Split *>(t->ws + L.split);
+    t->slist = reinterpret_cast<uint16_t *>(t->ws + L.slist);
+    e = cudaMemset(t->ws, 0, L.total);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) { cudaFree(t->ws); cudaFree(t->buckets); delete t; return cuda_err(e); }
+    *out = t;
+    return WRS_OK;
+}
+
+wrs_status wrs_table_build(wrs_table *t, const void *d_weights, uint64_t n, wrs_dtype dtype, void *stream)
+{
+    if (!t || !d_weights || n == 0 || n > t->cap) return WRS_EINVAL;
+    if (dtype != WRS_U32 && dtype != WRS_F32) return WRS_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_weights) % 4) != 0) return WRS_EINVAL;
+    return enqueue_build(t, d_weights, n, dtype, static_cast<cudaStream_t>(stream));
+}
+
+wrs_status wrs_build(const void *d_weights, uint64_t n, wrs_dtype dtype, void *stream, wrs_table **out)
+{
+    if (!out) return WRS_EINVAL;
+    *out = nullptr;
+    wrs_table *t = nullptr;
+    wrs_status st = wrs_table_create(n, &t);
+    if (st != WRS_OK) return st;
+    st = wrs_table_build(t, d_weights, n, dtype, stream);
+    if (st != WRS_OK) { wrs_table_free(t); return st; }
+    *out = t;
+    return WRS_OK;
+}
+
+wrs_status wrs_sample(const wrs_table *t, uint64_t k, uint64_t seed, uint64_t stream_id, uint32_t *d_out,
+                      void *stream)
+{
+    if (!t || t->n == 0) return WRS_EINVAL;
+    if (k == 0) return WRS_OK;
+    if (!d_out) return WRS_EINVAL;
+    if (t->host_status > 0) return (wrs_status)t->host_status;
+    const int sms = sm_count();
+    uint64_t want = (k + 256ull * kSampleUnroll - 1) / (256ull * kSampleUnroll);
+    uint64_t cap = (uint64_t)sms * 8;
+    const uint32_t blocks = (uint32_t)(want < cap ? (want < 1 ? 1 : want) : cap);
+    k_sample<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        t->buckets, t->n, t->hdr, k, (uint32_t)seed, (uint32_t)(seed >> 32), (uint32_t)stream_id,
+        (uint32_t)(stream_id >> 32), d_out);
+    return launch_err();
+}
+
+wrs_status wrs_table_build_host(wrs_table *t, const void *h_weights, uint64_t n, wrs_dtype dtype, void *stream)
+{
+    if (!t || !h_weights || n == 0 || n > t->cap) return WRS_EINVAL;
+    if (dtype != WRS_U32 && dtype != WRS_F32) return WRS_EINVAL;
+    const uint64_t bytes = n * 4;
+    if (t->stage_w_bytes < bytes) {
+        if (t->stage_w) { cudaDeviceSynchronize(); cudaFree(t->stage_w); t->stage_w = nullptr; t->stage_w_bytes = 0; }
+        cudaError_t e = cudaMalloc(&t->stage_w, bytes);
+        if (e != cudaSuccess) return cuda_err(e);
+        t->stage_w_bytes = bytes;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(t->stage_w, h_weights, bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_err(e);
+    return enqueue_build(t, t->stage_w, n, dtype, s);
+}
+
+wrs_status wrs_sample_host(wrs_table *t, uint64_t k, uint64_t seed, uint64_t stream_id, uint32_t *h_out,
+                           void *stream)
+{
+    if (!t || t->n == 0) return WRS_EINVAL;
+    if (k == 0) return WRS_OK;
+    if (!h_out) return WRS_EINVAL;
+    if (t->stage_out_cap < k) {
+        if (t->stage_out) { cudaDeviceSynchronize(); cudaFree(t->stage_out); t->stage_out = nullptr; t->stage_out_cap = 0; }
+        cudaError_t e = cudaMalloc(&t->stage_out, k * sizeof(uint32_t));
+        if (e != cudaSuccess) return cuda_err(e);
+        t->stage_out_cap = k;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    wrs_status st = wrs_sample(t, k, seed, stream_id, t->stage_out, stream);
+    if (st != WRS_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(h_out, t->stage_out, k * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return cuda_err(e);
+}
+
+wrs_status wrs_table_status(const wrs_table *t)
+{
+    if (!t) return WRS_EINVAL;
+    if (t->n == 0) return WRS_EINVAL;
+    uint32_t st = 0;
+    wrs_status e = read_status(t, &st);
+    if (e != WRS_OK) return e;
+    const_cast<wrs_table *>(t)->host_status = (int)st;
+    return (wrs_status)st;
+}
+
+wrs_status wrs_table_info_get(const wrs_table *t, wrs_table_info *info)
+{
+    if (!t || !info) return WRS_EINVAL;
+    if (t->n == 0) return WRS_EINVAL;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return WRS_EDEVICE;
+    DevHeader h;
+    e = cudaMemcpy(&h, t->hdr, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return WRS_EDEVICE;
+    info->n = t->n;
+    info->q_lo = h.q_lo;
+    info->q_hi = h.q_hi;
+    info->beta = h.beta;
+    info->shift = h.shift;
+    info->qp = h.qp;
+    info->n_light = h.n_light;
+    info->light_max = h.light_max;
+    info->status = (int32_t)h.status;
+    const_cast<wrs_table *>(t)->host_status = (int)h.status;
+    return WRS_OK;
+}
+
+const wrs_bucket *wrs_table_buckets(const wrs_table *t)
+{
+    return t ? reinterpret_cast<const wrs_bucket *>(t->buckets) : nullptr;
+}
+
+wrs_status wrs_table_download(const wrs_table *t, void *h_buckets, uint64_t bytes)
+{
+    if (!t || !h_buckets || t->n == 0 || bytes < t->n * sizeof(uint4)) return WRS_EINVAL;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(h_buckets, t->buckets, t->n * sizeof(uint4), cudaMemcpyDeviceToHost);
+    return cuda_err(e);
+}
+
+wrs_status wrs_table_upload(wrs_table *t, const void *h_buckets, uint64_t n, uint64_t q_lo, uint64_t q_hi,
+                            int32_t beta)
+{
+    if (!t || !h_buckets || n == 0 || n > t->cap) return WRS_EINVAL;
+    if ((q_lo | q_hi) == 0 || (q_hi >> 31) != 0) return WRS_EINVAL;
+    DevHeader h;
+    std::memset(&h, 0, sizeof(h));
+    unsigned __int128 Q = ((unsigned __int128)q_hi << 64) | q_lo;
+    int bits = 0;
+    for (unsigned __int128 v = Q; v; v >>= 1) ++bits;
+    int shift = bits > 64 ? bits - 64 : 0;
+    h.status = 0;
+    h.beta = beta;
+    h.shift = (uint32_t)shift;
+    h.q_lo = q_lo;
+    h.q_hi = q_hi;
+    h.qp = (uint64_t)(Q >> shift);
+    h.n = n;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(t->buckets, h_buckets, n * sizeof(uint4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(t->hdr, &h, sizeof(h), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_err(e);
+    t->n = n;
+    t->host_status = 0;
+    return WRS_OK;
+}
+
+wrs_status wrs_table_set_timing(wrs_table *t, int enable)
+{
+    if (!t) return WRS_EINVAL;
+    if (enable && !t->timing) {
+        for (int i = 0; i <= kStages; ++i) {
+            cudaError_t e = cudaEventCreate(&t->ev[i]);
+            if (e != cudaSuccess) {
+                for (int j = 0; j < i; ++j) cudaEventDestroy(t->ev[j]);
+                return cuda_err(e);
+            }
+        }
+        t->timing = 1;
+    } else if (!enable && t->timing) {
+        cudaDeviceSynchronize();
+        for (int i = 0; i <= kStages; ++i) cudaEventDestroy(t->ev[i]);
+        t->timing = 0;
+        t->timed_build = 0;
+    }
+    return WRS_OK;
+}
+
+wrs_status wrs_table_stage_ms(const wrs_table *t, float *ms, uint32_t count)
+{
+    if (!t || !ms || count == 0 || count > (uint32_t)kStages) return WRS_EINVAL;
+    if (!t->timing || !t->timed_build) return WRS_EINVAL;
+    cudaError_t e = cudaEventSynchronize(t->ev[kStages]);
+    for (uint32_t i = 0; e == cudaSuccess && i < count; ++i) e = cudaEventElapsedTime(&ms[i], t->ev[i], t->ev[i + 1]);
+    return cuda_err(e);
+}
+
+void wrs_table_free(wrs_table *t)
+{
+    if (!t) return;
+    cudaDeviceSynchronize();
+    if (t->timing)
+        for (int i = 0; i <= kStages; ++i) cudaEventDestroy(t->ev[i]);
+    cudaFree(t->ws);
+    cudaFree(t->buckets);
+    if (t->stage_w) cudaFree(t->stage_w);
+    if (t->stage_out) cudaFree(t->stage_out);
+    delete t;
+}
+
+const char *wrs_status_str(wrs_status s)
+{
+    switch (s) {
+    case WRS_OK: return "ok";
+    case WRS_EINVAL: return "invalid argument or weights";
+    case WRS_ENOMEM: return "out of memory";
+    case WRS_EOVERFLOW: return "exact weight sum exceeds 95 bits";
+    case WRS_ETIMEOUT: return "bounded device wait ran out";
+    case WRS_EDEVICE: return "CUDA runtime error";
+    case WRS_EINTERNAL: return "internal invariant failed";
+    }
+    return "unknown status";
+}
+
+uint32_t wrs_set_wait_limit(uint32_t polls)
+{
+    if (polls == 0) polls = 1;
+    return g_wait_limit.exchange(polls);
+}
+
+void wrs_debug_skip_publish(int64_t tile)
+{
+    g_skip_tile.store(tile);
+}
+
+} // extern "C"

@@ -99,3 +99,40 @@ def generate(kind: str, n: int, seed: int, s: float = 1.0) -> np.ndarray:
     if kind == "f32_zipf":
         return f32_zipf(n, s, seed)
     raise ValueError(kind)
+
+
+# --------------------------------------------------------------- device side
+KINDS = {"u32_uniform": 0, "f32_uniform": 1, "f32_zipf": 2}
+_wl = None
+
+
+def _wl_lib():
+    global _wl
+    if _wl is None:
+        import ctypes
+        import os
+
+        path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libwrs_workloads.so")
+        if not os.path.exists(path):
+            raise ImportError(f"{path} is missing: run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        lib.wl_generate.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
+                                    ctypes.c_double, ctypes.c_void_p]
+        lib.wl_generate.restype = ctypes.c_int
+        _wl = lib
+    return _wl
+
+
+def generate_device(kind: str, n: int, seed: int, s: float = 1.0, out=None, stream=None):
+    """Same recipe as ``generate`` but computed on the GPU into a torch tensor
+    (float32 for the f32 kinds, int32 words for u32_uniform)."""
+    import torch
+
+    dt = torch.int32 if kind == "u32_uniform" else torch.float32
+    if out is None:
+        out = torch.empty(n, dtype=dt, device="cuda")
+    st = torch.cuda.current_stream().cuda_stream if stream is None else stream
+    rc = _wl_lib().wl_generate(KINDS[kind], out.data_ptr(), n, seed, float(s), st)
+    if rc:
+        raise RuntimeError(f"wl_generate failed ({rc})")
+    return out

@@ -1,0 +1,263 @@
+"""Python binding of libwrs (ctypes; argument marshalling only).
+
+Every function has the name of the C entry point in ``include/wrs.h`` without
+the ``wrs_`` prefix and passes its arguments through unchanged: device
+pointers and streams are plain integers (``tensor.data_ptr()``,
+``torch.cuda.current_stream().cuda_stream``).  All computation happens in the
+CUDA kernels of ``libwrs.so``; there is no CPU fallback: importing this module
+without the built library raises.
+
+``AliasTable`` is a small convenience wrapper that owns a table handle and
+takes torch tensors (PyTorch is used only for device memory and streams).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libwrs.so")
+
+OK, EINVAL, ENOMEM, EOVERFLOW, ETIMEOUT, EDEVICE, EINTERNAL = range(7)
+U32, F32 = 0, 1
+BUCKET_BYTES = 16
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`"
+    )
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+
+class TableInfo(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_uint64),
+        ("q_lo", ctypes.c_uint64),
+        ("q_hi", ctypes.c_uint64),
+        ("beta", ctypes.c_int32),
+        ("shift", ctypes.c_uint32),
+        ("qp", ctypes.c_uint64),
+        ("n_light", ctypes.c_uint64),
+        ("light_max", ctypes.c_uint32),
+        ("status", ctypes.c_int32),
+    ]
+
+    @property
+    def Q(self) -> int:
+        return int(self.q_lo) | (int(self.q_hi) << 64)
+
+
+_P = ctypes.c_void_p
+_U64 = ctypes.c_uint64
+_I = ctypes.c_int
+_TBL = ctypes.c_void_p
+_PTBL = ctypes.POINTER(ctypes.c_void_p)
+
+_sig = {
+    "wrs_table_create": ([_U64, _PTBL], _I),
+    "wrs_table_build": ([_TBL, _P, _U64, _I, _P], _I),
+    "wrs_build": ([_P, _U64, _I, _P, _PTBL], _I),
+    "wrs_sample": ([_TBL, _U64, _U64, _U64, _P, _P], _I),
+    "wrs_table_build_host": ([_TBL, _P, _U64, _I, _P], _I),
+    "wrs_sample_host": ([_TBL, _U64, _U64, _U64, _P, _P], _I),
+    "wrs_table_status": ([_TBL], _I),
+    "wrs_table_info_get": ([_TBL, ctypes.POINTER(TableInfo)], _I),
+    "wrs_table_buckets": ([_TBL], _P),
+    "wrs_table_download": ([_TBL, _P, _U64], _I),
+    "wrs_table_upload": ([_TBL, _P, _U64, _U64, _U64, ctypes.c_int32], _I),
+    "wrs_table_set_timing": ([_TBL, _I], _I),
+    "wrs_table_stage_ms": ([_TBL, ctypes.POINTER(ctypes.c_float), ctypes.c_uint32], _I),
+    "wrs_table_free": ([_TBL], None),
+    "wrs_status_str": ([_I], ctypes.c_char_p),
+    "wrs_set_wait_limit": ([ctypes.c_uint32], ctypes.c_uint32),
+    "wrs_debug_skip_publish": ([ctypes.c_int64], None),
+}
+for _name, (_args, _res) in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+EXPORTED = tuple(_sig)
+
+
+class WrsError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {status_str(code)} ({code})")
+        self.code = code
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != OK:
+        raise WrsError(rc, where)
+
+
+def status_str(code: int) -> str:
+    return _lib.wrs_status_str(code).decode()
+
+
+# --- thin one-to-one wrappers (return the C status code) -------------------
+def table_create(capacity_n: int):
+    h = ctypes.c_void_p()
+    rc = _lib.wrs_table_create(capacity_n, ctypes.byref(h))
+    return rc, h.value
+
+
+def table_build(t, d_weights: int, n: int, dtype: int, stream: int = 0) -> int:
+    return _lib.wrs_table_build(t, d_weights, n, dtype, stream)
+
+
+def build(d_weights: int, n: int, dtype: int, stream: int = 0):
+    h = ctypes.c_void_p()
+    rc = _lib.wrs_build(d_weights, n, dtype, stream, ctypes.byref(h))
+    return rc, h.value
+
+
+def sample(t, k: int, seed: int, stream_id: int, d_out: int, stream: int = 0) -> int:
+    return _lib.wrs_sample(t, k, seed, stream_id, d_out, stream)
+
+
+def table_build_host(t, h_weights: int, n: int, dtype: int, stream: int = 0) -> int:
+    return _lib.wrs_table_build_host(t, h_weights, n, dtype, stream)
+
+
+def sample_host(t, k: int, seed: int, stream_id: int, h_out: int, stream: int = 0) -> int:
+    return _lib.wrs_sample_host(t, k, seed, stream_id, h_out, stream)
+
+
+def table_status(t) -> int:
+    return _lib.wrs_table_status(t)
+
+
+def table_info_get(t):
+    info = TableInfo()
+    rc = _lib.wrs_table_info_get(t, ctypes.byref(info))
+    return rc, info
+
+
+def table_buckets(t) -> int:
+    return _lib.wrs_table_buckets(t) or 0
+
+
+def table_download(t, h_buckets: int, nbytes: int) -> int:
+    return _lib.wrs_table_download(t, h_buckets, nbytes)
+
+
+def table_upload(t, h_buckets: int, n: int, q_lo: int, q_hi: int, beta: int) -> int:
+    return _lib.wrs_table_upload(t, h_buckets, n, q_lo, q_hi, beta)
+
+
+def table_set_timing(t, enable: bool) -> int:
+    return _lib.wrs_table_set_timing(t, 1 if enable else 0)
+
+
+STAGES = ("stats", "stats_combine", "classify", "tilescan", "split", "sweep")
+
+
+def table_stage_ms(t, count: int = 5):
+    buf = (ctypes.c_float * count)()
+    rc = _lib.wrs_table_stage_ms(t, buf, count)
+    return rc, [float(x) for x in buf]
+
+
+def table_free(t) -> None:
+    _lib.wrs_table_free(t)
+
+
+def set_wait_limit(polls: int) -> int:
+    return _lib.wrs_set_wait_limit(polls)
+
+
+def debug_skip_publish(tile: int) -> None:
+    _lib.wrs_debug_skip_publish(tile)
+
+
+# --- convenience wrapper over torch tensors --------------------------------
+def _dtype_code(t) -> int:
+    import torch
+
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype in (torch.uint32, torch.int32):
+        return U32
+    raise TypeError(f"weights must be float32 or uint32/int32 words, got {t.dtype}")
+
+
+def _stream_handle(stream) -> int:
+    import torch
+
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+class AliasTable:
+    """Owns one device-resident alias table (``wrs_table``)."""
+
+    def __init__(self, capacity_n: int):
+        rc, h = table_create(capacity_n)
+        _check(rc, "wrs_table_create")
+        self.handle = h
+        self.capacity = capacity_n
+        self.n = 0
+
+    def build(self, weights, stream=None) -> "AliasTable":
+        """weights: contiguous CUDA tensor of float32 or uint32/int32 words."""
+        assert weights.is_cuda and weights.is_contiguous()
+        n = weights.numel()
+        _check(table_build(self.handle, weights.data_ptr(), n, _dtype_code(weights), _stream_handle(stream)),
+               "wrs_table_build")
+        self.n = n
+        return self
+
+    def sample(self, k: int, seed: int, stream_id: int = 0, out=None, stream=None):
+        import torch
+
+        if out is None:
+            out = torch.empty(k, dtype=torch.int32, device="cuda")
+        assert out.is_cuda and out.is_contiguous() and out.numel() >= k and out.element_size() == 4
+        _check(sample(self.handle, k, seed, stream_id, out.data_ptr(), _stream_handle(stream)), "wrs_sample")
+        return out
+
+    def status(self) -> int:
+        return table_status(self.handle)
+
+    def set_timing(self, enable: bool = True) -> None:
+        _check(table_set_timing(self.handle, enable), "wrs_table_set_timing")
+
+    def stage_ms(self) -> dict:
+        rc, ms = table_stage_ms(self.handle, len(STAGES))
+        _check(rc, "wrs_table_stage_ms")
+        return dict(zip(STAGES, ms))
+
+    def info(self) -> TableInfo:
+        rc, info = table_info_get(self.handle)
+        _check(rc, "wrs_table_info_get")
+        return info
+
+    def download(self):
+        import numpy as np
+
+        buf = np.empty(self.n * 2, dtype=np.uint64)
+        _check(table_download(self.handle, buf.ctypes.data, buf.nbytes), "wrs_table_download")
+        words = buf.view(np.uint32).reshape(self.n, 4)
+        thr = buf.reshape(self.n, 2)[:, 0].copy()
+        alias = words[:, 2].copy()
+        return thr, alias, words[:, 3].copy()
+
+    def free(self) -> None:
+        if self.handle:
+            table_free(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.free()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

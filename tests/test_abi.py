@@ -1,0 +1,58 @@
+"""The C-ABI library loads, exports every entry point include/wrs.h declares,
+and rejects bad arguments before touching the GPU (runs without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def wrs():
+    import __graft_entry__ as g
+
+    g.build()
+    from paper_1903_00227_gb300 import wrs as W
+
+    return W
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "wrs.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(wrs_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(wrs):
+    names = declared_functions()
+    assert len(names) >= 15
+    lib = ctypes.CDLL(wrs.LIB_PATH)
+    for name in names:
+        assert hasattr(lib, name), name
+    assert sorted(wrs.EXPORTED) == names
+
+
+def test_argument_errors_need_no_gpu(wrs):
+    rc, h = wrs.table_create(0)
+    assert rc == wrs.EINVAL and h is None
+    rc, h = wrs.table_create(1 << 32)
+    assert rc == wrs.EINVAL
+    assert wrs.table_build(None, 0, 10, wrs.U32, 0) == wrs.EINVAL
+    assert wrs.sample(None, 10, 1, 0, 0, 0) == wrs.EINVAL
+    assert wrs.table_status(None) == wrs.EINVAL
+    assert wrs.table_download(None, 0, 0) == wrs.EINVAL
+    assert wrs.table_buckets(None) == 0
+    wrs.table_free(None)
+
+
+def test_status_strings(wrs):
+    seen = {wrs.status_str(c) for c in range(7)}
+    assert len(seen) == 7
+    assert wrs.status_str(99) == "unknown status"
+
+
+def test_bucket_layout_matches_header():
+    text = open(os.path.join(ROOT, "include", "wrs.h")).read()
+    assert re.search(r"uint64_t thr;\s*uint32_t alias;\s*uint32_t reserved;", text)

@@ -1,0 +1,191 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Tables must be identical bucket for bucket (thresholds and aliases) to the
+oracle's Alg. 2 table, the header (Q, beta, shift, qp, light count) must match
+the oracle's exact units, and samples must be identical index for index to
+the oracle's queries (integer work: bit-exact).  Sizes span several 4096-item
+tiles with ragged tails; inputs include the paper's workload shapes
+(uniform, Zipf-permuted) and degenerate ones.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import wrs_oracle as O
+from paper_1903_00227_gb300 import workloads as WL
+from paper_1903_00227_gb300 import wrs
+from tests import _gpu as G
+
+pytestmark = pytest.mark.gpu
+
+TILE = 2048
+SCAN_CHUNK = 256 * TILE
+
+
+def _inputs():
+    rng = np.random.default_rng(123)
+    cases = []
+    for n in (1, 2, 3, 17, TILE - 1, TILE, TILE + 1, 2 * TILE + 5, 3 * TILE + 17, 100_003):
+        cases.append((f"u32_uniform_{n}", WL.u32_uniform(n, n)))
+        cases.append((f"f32_uniform_{n}", WL.f32_uniform(n, n + 1)))
+        cases.append((f"zipf1_{n}", WL.f32_zipf(n, 1.0, n + 2)))
+    for s in (0.5, 0.8, 1.5, 2.0, 3.0):
+        cases.append((f"zipf{s}_60000", WL.f32_zipf(60_000, s, 7)))
+    n = 50_000
+    base = WL.u32_uniform(n, 9)
+    cases.append(("sorted_asc", np.sort(base)))
+    cases.append(("sorted_desc", np.sort(base)[::-1].copy()))
+    cases.append(("all_equal", np.full(n, 77, np.uint32)))
+    cases.append(("all_equal_f32", np.full(n, 0.1, np.float32)))
+    g = np.ones(n, np.uint32)
+    g[n // 3] = 10_000_000
+    cases.append(("one_giant", g))
+    cases.append(("small_ints_with_zeros", rng.integers(0, 4, n).astype(np.uint32)))
+    z = np.zeros(n, np.uint32)
+    z[::97] = 5
+    cases.append(("mostly_zero", z))
+    tv = np.where(rng.random(n) < 0.1, 9, 1).astype(np.uint32)
+    cases.append(("two_values", tv))
+    wide = (rng.random(n) * np.exp2(rng.integers(-30, 20, n))).astype(np.float32)
+    cases.append(("f32_wide_range", wide))
+    sub = (rng.integers(1, 1 << 23, n) * 2.0 ** -149).astype(np.float32)
+    cases.append(("f32_subnormal", sub))
+    heavy_first = np.concatenate([np.full(n // 10, 1000, np.uint32), np.ones(n - n // 10, np.uint32)])
+    cases.append(("heavies_first", heavy_first))
+    cases.append(("heavies_last", heavy_first[::-1].copy()))
+    return cases
+
+
+CASES = _inputs()
+
+
+@pytest.mark.parametrize("name,w", CASES, ids=[c[0] for c in CASES])
+def test_table_and_samples_match_oracle(name, w):
+    qz, tab = O.build_table(w)
+    n = len(w)
+    with G.gpu_build(w) as t:
+        assert t.status() == wrs.OK
+        info = t.info()
+        assert info.Q == qz.Q and info.beta == qz.beta
+        assert info.shift == tab.shift and info.qp == tab.Qp
+        n_light = sum(1 for i in range(n) if n * qz.q_int(i) <= qz.Q) if n < 5000 else None
+        if n_light is not None:
+            assert info.n_light == n_light
+        thr, alias, res = t.download()
+        bad = np.nonzero((thr != tab.thr) | (alias != tab.alias))[0]
+        assert bad.size == 0, f"{bad.size} buckets differ, first {bad[:5]}: gpu {thr[bad[:3]]},{alias[bad[:3]]} oracle {tab.thr[bad[:3]]},{tab.alias[bad[:3]]}"
+        assert not res.any()
+        k = 3 * n + 7
+        got = G.gpu_samples(t, k, seed=1000 + n, stream_id=5)
+        want = O.sample(tab.thr, tab.alias, tab.Qp, k, 1000 + n, 5)
+        assert np.array_equal(got, want)
+
+
+def test_config1_exact_workload():
+    """n = 10^6 uint32 weights uniform in [1, 2^24] from seed 1, then 10^6
+    samples with seed 2: table and indices bit-exact."""
+    w = WL.u32_uniform(1_000_000, 1)
+    qz, tab = O.build_table(w)
+    with G.gpu_build(w) as t:
+        thr, alias, _ = t.download()
+        assert np.array_equal(thr, tab.thr) and np.array_equal(alias, tab.alias)
+        got = G.gpu_samples(t, 1_000_000, seed=2)
+    assert np.array_equal(got, O.sample(tab.thr, tab.alias, tab.Qp, 1_000_000, 2, 0))
+
+
+def test_rebuild_same_table_object():
+    with wrs.AliasTable(3 * TILE) as t:
+        for seed, n in ((1, 3 * TILE), (2, 1000), (3, 2 * TILE + 1)):
+            w = WL.f32_zipf(n, 1.0, seed)
+            qz, tab = O.build_table(w)
+            t.build(G.to_device(w))
+            thr, alias, _ = t.download()
+            assert np.array_equal(thr, tab.thr) and np.array_equal(alias, tab.alias)
+
+
+def test_sampler_alone_on_uploaded_oracle_table():
+    w = WL.f32_zipf(30_000, 1.2, 5)
+    qz, tab = O.build_table(w)
+    n = len(w)
+    buckets = np.zeros((n, 2), np.uint64)
+    buckets[:, 0] = tab.thr
+    buckets[:, 1] = tab.alias.astype(np.uint64)
+    with wrs.AliasTable(n) as t:
+        rc = wrs.table_upload(t.handle, buckets.ctypes.data, n, int(qz.Qw[0]), int(qz.Qw[1]), qz.beta)
+        assert rc == wrs.OK
+        t.n = n
+        for seed, sid in ((0, 0), (7, 1), (2 ** 63 + 5, 2 ** 40 + 3)):
+            got = G.gpu_samples(t, 123_457, seed, sid)
+            assert np.array_equal(got, O.sample(tab.thr, tab.alias, tab.Qp, 123_457, seed, sid))
+
+
+@pytest.mark.parametrize("bad,code", [(np.nan, wrs.EINVAL), (np.inf, wrs.EINVAL), (-1.0, wrs.EINVAL),
+                                      (-0.0, wrs.EINVAL)])
+def test_invalid_weights_reported(bad, code):
+    w = WL.f32_uniform(10_000, 3)
+    w[7777] = bad
+    with G.gpu_build(w) as t:
+        # sampling before the status is read: the kernel writes nothing
+        out = torch.full((100,), -7, dtype=torch.int32, device="cuda")
+        t.sample(100, 1, out=out)
+        torch.cuda.synchronize()
+        assert (out == -7).all(), "a failed table must not be sampled"
+        assert t.status() == code
+        # once the host has read the failure, the call returns it
+        with pytest.raises(wrs.WrsError) as e:
+            t.sample(100, 1, out=out)
+        assert e.value.code == code
+
+
+def test_all_zero_and_overflow_reported():
+    with G.gpu_build(np.zeros(5000, np.float32)) as t:
+        assert t.status() == wrs.EINVAL
+    w = np.ones(5000, np.float32)
+    w[0] = np.float32(2.0 ** -149)
+    w[1] = np.float32(2.0 ** 100)
+    with G.gpu_build(w) as t:
+        assert t.status() == wrs.EOVERFLOW
+
+
+def test_bounded_wait_times_out_and_context_survives():
+    """A tile that never publishes its look-back flag makes its successor's
+    bounded wait run out: the build reports WRS_ETIMEOUT instead of hanging,
+    and the same table then builds correctly."""
+    w = WL.u32_uniform(5 * SCAN_CHUNK + 17, 4)
+    with wrs.AliasTable(len(w)) as t:
+        old = wrs.set_wait_limit(2000)
+        try:
+            wrs.debug_skip_publish(2)
+            t.build(G.to_device(w))
+            assert t.status() == wrs.ETIMEOUT
+        finally:
+            wrs.set_wait_limit(old)
+            wrs.debug_skip_publish(-1)
+        t.build(G.to_device(w))
+        assert t.status() == wrs.OK
+        qz, tab = O.build_table(w)
+        thr, alias, _ = t.download()
+        assert np.array_equal(thr, tab.thr) and np.array_equal(alias, tab.alias)
+
+
+def test_unaligned_weight_pointer():
+    w = WL.f32_zipf(3 * TILE + 3, 1.0, 11)
+    big = torch.from_numpy(np.concatenate([np.zeros(1, np.float32), w])).cuda()
+    view = big[1:]
+    assert view.data_ptr() % 16 != 0
+    qz, tab = O.build_table(w)
+    with wrs.AliasTable(len(w)) as t:
+        t.build(view)
+        thr, alias, _ = t.download()
+    assert np.array_equal(thr, tab.thr) and np.array_equal(alias, tab.alias)
+
+
+def test_host_buffer_entry_points():
+    w = WL.f32_uniform(20_000, 8)
+    qz, tab = O.build_table(w)
+    with wrs.AliasTable(len(w)) as t:
+        assert wrs.table_build_host(t.handle, w.ctypes.data, len(w), wrs.F32, 0) == wrs.OK
+        t.n = len(w)
+        out = np.zeros(50_000, np.uint32)
+        assert wrs.sample_host(t.handle, 50_000, 9, 1, out.ctypes.data, 0) == wrs.OK
+    assert np.array_equal(out, O.sample(tab.thr, tab.alias, tab.Qp, 50_000, 9, 1))
