@@ -87,8 +87,28 @@ int sm_count()
     return sms > 0 ? sms : 1;
 }
 
+bool g_attr_done[64];
+
+wrs_status set_kernel_attributes()
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return WRS_EDEVICE;
+    if (g_attr_done[dev]) return WRS_OK;
+    const int bytes = (int)sizeof(SweepSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_sweep<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sweep<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return WRS_EDEVICE;
+    g_attr_done[dev] = true;
+    return WRS_OK;
+}
+
 wrs_status enqueue_build(wrs_table *t, const void *d_weights, uint64_t n, wrs_dtype dtype, cudaStream_t s)
 {
+    {
+        const wrs_status st = set_kernel_attributes();
+        if (st != WRS_OK) return st;
+    }
     const uint32_t *w = static_cast<const uint32_t *>(d_weights);
     const int vec = (reinterpret_cast<uintptr_t>(w) % 16) == 0;
     const uint32_t ntiles = (uint32_t)((n + kTile - 1) / kTile);
@@ -123,8 +143,10 @@ wrs_status enqueue_build(wrs_table *t, const void *d_weights, uint64_t n, wrs_dt
     if (tm) cudaEventRecord(t->ev[4], s);
     k_split<<<(ntiles + kThreads - 1) / kThreads, kThreads, 0, s>>>(t->incl, ntiles, n, t->hdr, t->split);
     if (tm) cudaEventRecord(t->ev[5], s);
-    if (f32) k_sweep<1><<<ntiles, kThreads, 0, s>>>(w, n, vec, t->hdr, t->incl, t->split, t->slist, ntiles, t->buckets);
-    else k_sweep<0><<<ntiles, kThreads, 0, s>>>(w, n, vec, t->hdr, t->incl, t->split, t->slist, ntiles, t->buckets);
+    const size_t sweep_smem = sizeof(SweepSmem);
+    const uint32_t sweep_blocks = (ntiles + kSweepTiles - 1) / kSweepTiles;
+    if (f32) k_sweep<1><<<sweep_blocks, kThreads, sweep_smem, s>>>(w, n, vec, t->hdr, t->incl, t->split, t->slist, ntiles, t->buckets);
+    else k_sweep<0><<<sweep_blocks, kThreads, sweep_smem, s>>>(w, n, vec, t->hdr, t->incl, t->split, t->slist, ntiles, t->buckets);
     if (tm) cudaEventRecord(t->ev[6], s);
     t->timed_build = tm;
     wrs_status st = launch_err();

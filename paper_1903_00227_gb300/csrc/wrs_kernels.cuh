@@ -93,34 +93,42 @@ __device__ __forceinline__ void acc_merge(Acc &a, const Acc &b)
     if (hi64(a.acc) >> (kQBits - 64)) a.flags |= kPartOverflow;
 }
 
+// Add one weight.  Addends below 2^61 (shift <= 37) go to the 64-bit side
+// accumulator a64, which the caller folds into acc at least every 8 items.
 template <int F32>
-__device__ __forceinline__ void acc_take(Acc &a, uint32_t x)
+__device__ __forceinline__ void acc_take(Acc &a, uint64_t &a64, uint32_t x)
 {
-    if (!F32) { a.acc += x; return; }
-    uint32_t ex = (x >> 23) & 0xFFu;
+    if (!F32) { a64 += x; return; }
+    const uint32_t ex = (x >> 23) & 0xFFu;
     if ((x >> 31) || ex == 0xFFu) { a.flags |= kPartInvalid; return; }
     uint32_t m = x & 0x7FFFFFu;
     if (ex) m |= 0x800000u;
     if (!m) return;
-    int e = (ex ? (int)ex : 1) - 150;
-    int lsb = e + __ffs(m) - 1;
-    if (lsb < a.base) {
+    const int e = (ex ? (int)ex : 1) - 150;
+    const int lsb = e + __ffs(m) - 1;
+    if (lsb < a.base) { // rare: a lower set bit than any before; rebase
+        a.acc += a64;
+        a64 = 0;
         if (a.acc) {
-            int d = a.base - lsb;
+            const int d = a.base - lsb;
             if (bitlen128(a.acc) + d > kQBits) { a.flags |= kPartOverflow; a.acc = 0; }
             else a.acc <<= d;
         }
         a.base = lsb;
     }
-    int sh = e - a.base;
-    u128 q;
-    if (sh >= 0) {
-        if ((32 - __clz(m)) + sh > kQBits) { a.flags |= kPartOverflow; return; }
-        q = (u128)m << sh;
+    const int sh = e - a.base;
+    if (sh <= 37) {
+        a64 += sh >= 0 ? ((uint64_t)m << sh) : (uint64_t)(m >> (-sh));
     } else {
-        q = (u128)(m >> (-sh));
+        if ((32 - __clz(m)) + sh > kQBits) { a.flags |= kPartOverflow; return; }
+        a.acc += (u128)m << sh;
     }
-    a.acc += q;
+}
+
+__device__ __forceinline__ void acc_fold(Acc &a, uint64_t &a64)
+{
+    a.acc += a64;
+    a64 = 0;
     if (hi64(a.acc) >> (kQBits - 64)) { a.flags |= kPartOverflow; a.acc = 0; }
 }
 
@@ -168,23 +176,31 @@ __global__ void __launch_bounds__(kThreads) k_stats(const uint32_t *__restrict__
     a.base = F32 ? INT_MAX : 0;
     a.acc = 0;
     a.flags = 0;
+    uint64_t a64 = 0;
     const uint64_t tid = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
     const uint64_t nth = (uint64_t)gridDim.x * kThreads;
     const uint64_t nv = vec ? n / 4 : 0;
     const uint4 *w4 = reinterpret_cast<const uint4 *>(w);
     uint64_t i = tid;
     for (; i + 3 * nth < nv; i += 4 * nth) {
-        uint4 v0 = __ldg(w4 + i), v1 = __ldg(w4 + i + nth), v2 = __ldg(w4 + i + 2 * nth), v3 = __ldg(w4 + i + 3 * nth);
-        acc_take<F32>(a, v0.x); acc_take<F32>(a, v0.y); acc_take<F32>(a, v0.z); acc_take<F32>(a, v0.w);
-        acc_take<F32>(a, v1.x); acc_take<F32>(a, v1.y); acc_take<F32>(a, v1.z); acc_take<F32>(a, v1.w);
-        acc_take<F32>(a, v2.x); acc_take<F32>(a, v2.y); acc_take<F32>(a, v2.z); acc_take<F32>(a, v2.w);
-        acc_take<F32>(a, v3.x); acc_take<F32>(a, v3.y); acc_take<F32>(a, v3.z); acc_take<F32>(a, v3.w);
+        const uint4 v0 = __ldg(w4 + i), v1 = __ldg(w4 + i + nth), v2 = __ldg(w4 + i + 2 * nth), v3 = __ldg(w4 + i + 3 * nth);
+        acc_take<F32>(a, a64, v0.x); acc_take<F32>(a, a64, v0.y); acc_take<F32>(a, a64, v0.z); acc_take<F32>(a, a64, v0.w);
+        acc_take<F32>(a, a64, v1.x); acc_take<F32>(a, a64, v1.y); acc_take<F32>(a, a64, v1.z); acc_take<F32>(a, a64, v1.w);
+        if (F32) acc_fold(a, a64);
+        acc_take<F32>(a, a64, v2.x); acc_take<F32>(a, a64, v2.y); acc_take<F32>(a, a64, v2.z); acc_take<F32>(a, a64, v2.w);
+        acc_take<F32>(a, a64, v3.x); acc_take<F32>(a, a64, v3.y); acc_take<F32>(a, a64, v3.z); acc_take<F32>(a, a64, v3.w);
+        if (F32) acc_fold(a, a64);
     }
     for (; i < nv; i += nth) {
-        uint4 v = __ldg(w4 + i);
-        acc_take<F32>(a, v.x); acc_take<F32>(a, v.y); acc_take<F32>(a, v.z); acc_take<F32>(a, v.w);
+        const uint4 v = __ldg(w4 + i);
+        acc_take<F32>(a, a64, v.x); acc_take<F32>(a, a64, v.y); acc_take<F32>(a, a64, v.z); acc_take<F32>(a, a64, v.w);
+        if (F32) acc_fold(a, a64);
     }
-    for (uint64_t j = nv * 4 + tid; j < n; j += nth) acc_take<F32>(a, __ldg(w + j));
+    for (uint64_t j = nv * 4 + tid; j < n; j += nth) {
+        acc_take<F32>(a, a64, __ldg(w + j));
+        if (F32) acc_fold(a, a64);
+    }
+    acc_fold(a, a64);
     a = acc_block_reduce(a);
     if (threadIdx.x == 0) {
         Partial p;
@@ -260,6 +276,17 @@ __global__ void __launch_bounds__(kThreads) k_stats_combine(const Partial *__res
 }
 
 // ---------------------------------------------------------- k_classify
+// q of a weight known to be below 2^61 (shift <= 37)
+__device__ __forceinline__ uint64_t q64_of(uint32_t x, uint32_t f32, int beta)
+{
+    if (!f32) return x;
+    const uint32_t ex = (x >> 23) & 0xFFu;
+    uint32_t m = x & 0x7FFFFFu;
+    if (ex) m |= 0x800000u;
+    const int sh = (ex ? (int)ex : 1) - 150 - beta;
+    return sh >= 0 ? ((uint64_t)m << sh) : (uint64_t)(m >> (-sh));
+}
+
 // One 2048-weight tile per iteration of a grid-stride loop (no dependency
 // between tiles): light count, light and heavy sums, the tile's heavy count
 // and first heavy offset, and -- when one class has at most 32 members in the
@@ -288,59 +315,93 @@ __global__ void __launch_bounds__(kThreads) k_classify(const uint32_t *__restric
                                                        const DevHeader *__restrict__ hdr, TileSum *__restrict__ agg,
                                                        uint16_t *__restrict__ slist, uint32_t ntiles)
 {
-    __shared__ U2 s_scan[kWarps];
+    __shared__ u128 s_l[kWarps], s_h[kWarps];
+    __shared__ uint32_t s_c[kWarps], s_first[kWarps];
     __shared__ uint32_t s_cnt[kWarps];
-    __shared__ uint32_t s_first[kWarps];
     if (*(volatile const uint32_t *)&hdr->status) return;
     const uint32_t light_max = hdr->light_max;
     const int beta = hdr->beta;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const uint64_t tile0 = (uint64_t)t * kTile;
-        const uint64_t first = tile0 + (uint64_t)threadIdx.x * kItems;
-        uint32_t x[kItems];
-        load_items(w, n, vec, first, x);
-        uint32_t cl = 0, nh = 0, fh = kNone;
-        u128 L = 0, H = 0;
+    uint32_t t = blockIdx.x;
+    uint32_t x[kItems];
+    if (t < ntiles) load_items(w, n, vec, (uint64_t)t * kTile + (uint64_t)threadIdx.x * kItems, x);
+    for (; t < ntiles; t += gridDim.x) {
+        const uint64_t first = (uint64_t)t * kTile + (uint64_t)threadIdx.x * kItems;
+        uint32_t cl = 0, nh = 0, fh = kNone, lm = 0;
+        // exact sums: 64-bit when every addend is below 2^61, else 128-bit
+        bool narrow = true;
 #pragma unroll
         for (int k = 0; k < kItems; ++k) {
-            if (first + k < n) {
-                const u128 q = q_of(x[k], F32, beta);
-                if (x[k] <= light_max) { ++cl; L += q; }
-                else { ++nh; H += q; if (fh == kNone) fh = threadIdx.x * kItems + k; }
+            const bool valid = first + k < n;
+            if (valid && x[k] <= light_max) { ++cl; lm |= 1u << k; }
+            else if (valid) { ++nh; if (fh == kNone) fh = threadIdx.x * kItems + k; }
+            if (F32 && valid) {
+                const uint32_t ex = (x[k] >> 23) & 0xFFu;
+                if ((ex ? (int)ex : 1) - 150 - beta > 37) narrow = false;
             }
         }
-        U2 tot;
-        block_exclusive_scan2(U2{L, H}, tot, s_scan);
-        uint32_t ctot;
-        const uint32_t cex = block_exclusive_scan_u32(cl | (nh << 16), ctot, s_cnt);
-        uint32_t f = fh;
+        u128 L, H;
+        if (narrow) {
+            uint64_t l64 = 0, h64 = 0;
 #pragma unroll
-        for (int d = 16; d > 0; d >>= 1) f = min(f, __shfl_xor_sync(0xFFFFFFFFu, f, d));
-        if (lane == 0) s_first[wid] = f;
+            for (int k = 0; k < kItems; ++k) {
+                if (first + k < n) {
+                    const uint64_t q = q64_of(x[k], F32, beta);
+                    if ((lm >> k) & 1u) l64 += q; else h64 += q;
+                }
+            }
+            L = l64; H = h64;
+        } else {
+            L = 0; H = 0;
+#pragma unroll
+            for (int k = 0; k < kItems; ++k) {
+                if (first + k < n) {
+                    const u128 q = q_of(x[k], F32, beta);
+                    if ((lm >> k) & 1u) L += q; else H += q;
+                }
+            }
+        }
+        const uint32_t lm_keep = lm;
+        const uint32_t cl_keep = cl, nh_keep = nh;
+        // prefetch the next tile of this block
+        const uint32_t tn = t + gridDim.x;
+        if (tn < ntiles) load_items(w, n, vec, (uint64_t)tn * kTile + (uint64_t)threadIdx.x * kItems, x);
+        // block reduction of (L, H, counts, first heavy)
+        uint32_t cc = cl | (nh << 16), f = fh;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            L += shfl_down128(L, d);
+            H += shfl_down128(H, d);
+            cc += __shfl_down_sync(0xFFFFFFFFu, cc, d);
+            f = min(f, __shfl_down_sync(0xFFFFFFFFu, f, d));
+        }
+        if (lane == 0) { s_l[wid] = L; s_h[wid] = H; s_c[wid] = cc; s_first[wid] = f; }
         __syncthreads();
+        uint32_t ctot = 0;
+#pragma unroll
+        for (int i = 0; i < kWarps; ++i) ctot += s_c[i];
         const uint32_t tot_l = ctot & 0xFFFFu, tot_h = ctot >> 16;
         if (threadIdx.x == 0) {
+            u128 lt = 0, ht = 0;
             TileSum a;
-            a.l_lo = lo64(tot.a); a.l_hi = hi64(tot.a); a.h_lo = lo64(tot.b); a.h_hi = hi64(tot.b);
-            a.cl = tot_l; a.nheavy = tot_h; a.first_heavy = kNone; a.pad = 0;
+            a.first_heavy = kNone;
 #pragma unroll
-            for (int i = 0; i < kWarps; ++i) a.first_heavy = min(a.first_heavy, s_first[i]);
+            for (int i = 0; i < kWarps; ++i) { lt += s_l[i]; ht += s_h[i]; a.first_heavy = min(a.first_heavy, s_first[i]); }
+            a.l_lo = lo64(lt); a.l_hi = hi64(lt); a.h_lo = lo64(ht); a.h_hi = hi64(ht);
+            a.cl = tot_l; a.nheavy = tot_h; a.pad = 0;
             tilesum_st(agg + t, a);
         }
         // member list of a sparse class (heavies first)
         const bool list_heavy = tot_h <= (uint32_t)kSparse;
         const bool list_light = !list_heavy && tot_l <= (uint32_t)kSparse;
         if (list_heavy || list_light) {
-            uint32_t slot = list_heavy ? (cex >> 16) : (cex & 0xFFFFu);
+            uint32_t ctot2;
+            uint32_t slot = block_exclusive_scan_u32(list_heavy ? nh_keep : cl_keep, ctot2, s_cnt);
 #pragma unroll
             for (int k = 0; k < kItems; ++k) {
-                if (first + k < n) {
-                    const bool is_light = x[k] <= light_max;
-                    if (is_light == list_light) {
-                        slist[(uint64_t)t * kSparse + slot] = (uint16_t)(threadIdx.x * kItems + k);
-                        ++slot;
-                    }
+                if (first + k < n && (((lm_keep >> k) & 1u) != 0) == list_light) {
+                    slist[(uint64_t)t * kSparse + slot] = (uint16_t)(threadIdx.x * kItems + k);
+                    ++slot;
                 }
             }
         }
@@ -538,75 +599,111 @@ __global__ void __launch_bounds__(kThreads) k_split(const TileSum *__restrict__ 
     split[c] = s;
 }
 
-__device__ __forceinline__ uint32_t upper_bound_keys(const u128 *key, uint32_t cnt, u128 v)
-{ // first index with key > v
-    uint32_t lo = 0, hi = cnt;
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (key[mid] <= v) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
 
-__device__ __forceinline__ uint32_t lower_bound_keys(const u128 *key, uint32_t cnt, u128 v)
-{ // first index with key >= v
-    uint32_t lo = 0, hi = cnt;
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (key[mid] < v) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
 
 // ------------------------------------------------------------ k_sweep
 // Tile c packs, as Alg. 3's pack does for one subproblem, the buckets of its
 // own lights and of every heavy item whose key E lies in (D_c, D_c'] (D_c:
-// key of the tile's first light, D_c': key after its last light), i.e. the
-// heavy items Alg. 2 packs while it consumes this tile's lights.  The heavy
-// items come in index order from the tile k_split named (the split of Alg. 3
-// on the heavy prefix sums) into a window in shared memory (keys and
-// positions); the first two tiles of that stream are loaded together with the
-// own tile.  Thread t owns 8 consecutive items; with K_t the key of its first
-// light and K_t' the key after its last, it resolves
-//   its lights:  alias = first heavy with E > D (the current heavy);
-//   the heavies with E in (K_t, K_t']:  bucket Q - (D_next - E), D_next = key
-//                of the first light with D >= E, alias = the next heavy.
-// A stream longer than the window is consumed in rounds.
-struct Win {
-    u128 key[kTile];
-    uint32_t pos[kTile];
-    uint32_t count;
-    uint32_t done;       // the last entry ends the stream
-    uint32_t tile;       // next stream tile
-    uint32_t pad;
-    uint64_t next_rank;  // heavy rank of the next entry to take
+// key of the tile's first light, D_c': key after its last light): exactly
+// the items Alg. 2 packs while it consumes this tile's lights.  The heavy
+// items come tile by tile in index order from the tile k_split named
+// (Alg. 3's split on the heavy prefix sums); the first such tile is loaded
+// together with the own tile.  For each stream tile the block merges, in key
+// order, the own lights whose current heavy lies in that tile with the
+// tile's heavies in (D_c, D_c'] (heavy first when E <= D): a light step
+// takes the current heavy as its alias, a heavy step gets bucket
+// Q - (D_next - E) with D_next the key of the next light, and the next heavy
+// as alias.  The merged sequence is split evenly over the threads by a
+// merge-path co-rank search, then each thread walks its slice.
+__device__ __forceinline__ u128 nq_of(uint32_t x, uint32_t f32, int beta, uint32_t n32)
+{
+    if (!f32) return (u128)((uint64_t)x * n32);
+    const uint32_t ex = (x >> 23) & 0xFFu;
+    uint32_t m = x & 0x7FFFFFu;
+    if (ex) m |= 0x800000u;
+    const uint64_t nm = (uint64_t)m * n32; // < 2^56
+    const int sh = (ex ? (int)ex : 1) - 150 - beta;
+    return sh >= 0 ? ((u128)nm << sh) : (u128)(nm >> (-sh)); // exact: m carries the low zero bits
+}
+
+__device__ __forceinline__ u128 block_exclusive_scan1(u128 v, u128 &total, u128 *sm)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    u128 inc = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const u128 o = shfl_up128(inc, d);
+        if (lane >= d) inc += o;
+    }
+    if (lane == 31) sm[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        u128 t = lane < kWarps ? sm[lane] : (u128)0;
+#pragma unroll
+        for (int d = 1; d < kWarps; d <<= 1) {
+            const u128 o = shfl_up128(t, d);
+            if (lane >= d) t += o;
+        }
+        if (lane < kWarps) sm[lane] = t;
+    }
+    __syncthreads();
+    const u128 base = wid ? sm[wid - 1] : (u128)0;
+    total = sm[kWarps - 1];
+    __syncthreads();
+    return base + inc - v;
+}
+
+// 16-B elements, 8 per 128-B bank row: XOR the column with the row's low bits
+// so that threads reading consecutive rows at one column hit distinct banks.
+__device__ __forceinline__ uint32_t swz(uint32_t j) { return j ^ ((j >> 3) & 7u); }
+
+struct SweepSmem {
+    u128 okey[kTile];     // keys D of the own lights, in order (swizzled)
+    u128 hkey[kTile];     // keys E of the current stream tile's heavies (swizzled)
+    uint16_t ooff[kTile]; // offsets of the own lights in the tile
+    uint16_t hoff[kTile]; // offsets of the stream tile's heavies
+    u128 scan[kWarps];
+    uint32_t cnt[kWarps];
+    uint32_t hcount;
+    uint32_t rng[4];      // light and heavy index ranges of the current round
 };
 
-// Append heavies of stream tile t (words in x, loaded by the caller) to W:
-// ranks >= W.next_rank with key > lo, up to and including the first key > hi,
-// while W has room.  All threads call.
+__device__ __forceinline__ uint32_t ub_keys(const u128 *key, uint32_t lo, uint32_t hi, u128 v)
+{ // first index in [lo, hi) with key > v
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (key[swz(mid)] <= v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ uint32_t lb_keys(const u128 *key, uint32_t lo, uint32_t hi, u128 v)
+{ // first index in [lo, hi) with key >= v
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (key[swz(mid)] < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Keys of stream tile t's heavies into S.hkey/S.hoff (all threads call).
 template <int F32>
-__device__ void stream_tile(Win &W, uint32_t t, const uint32_t (&x)[kItems], uint64_t n, const TileSum *incl,
-                            const uint16_t *__restrict__ slist, const uint32_t *__restrict__ w, u128 Q,
-                            uint32_t light_max, int beta, u128 lo, u128 hi, U2 *s_scan,
-                            unsigned long long *s_min)
+__device__ __forceinline__ void load_heavies(SweepSmem &S, uint32_t t, const uint32_t (&y)[kItems], uint32_t nheavy,
+                                             uint64_t n, uint32_t n32, const TileSum *incl,
+                                             const uint16_t *__restrict__ slist, const uint32_t *__restrict__ w,
+                                             u128 Q, uint32_t light_max, int beta)
 {
     const Prefix pf = prefix_at(incl, t, n);
     const u128 base = key_E(pf, n, Q);
-    const uint64_t rank0 = pf.ch;
     const uint64_t tile0 = (uint64_t)t * kTile;
-    const uint32_t nheavy = tilesum_ldcg(incl + t).nheavy;
-    const uint32_t count = W.count;
-    const uint64_t next_rank = W.next_rank;
-    const uint32_t room = (uint32_t)kTile - count;
-    if (nheavy <= (uint32_t)kSparse) { // member list: one warp
+    if (nheavy <= (uint32_t)kSparse) {
         if (threadIdx.x < 32) {
             const int lane = threadIdx.x;
             u128 d = 0;
             uint32_t off = 0;
             if ((uint32_t)lane < nheavy) {
                 off = slist[(uint64_t)t * kSparse + lane];
-                d = times_n(q_of(__ldg(w + tile0 + off), F32, beta), n) - Q;
+                d = nq_of(__ldg(w + tile0 + off), F32, beta, n32) - Q;
             }
             u128 key = d;
 #pragma unroll
@@ -614,29 +711,8 @@ __device__ void stream_tile(Win &W, uint32_t t, const uint32_t (&x)[kItems], uin
                 const u128 o = shfl_up128(key, s);
                 if (lane >= s) key += o;
             }
-            key += base;
-            const uint64_t r = rank0 + lane;
-            const bool mem = (uint32_t)lane < nheavy;
-            const bool keep = mem && r >= next_rank && key > lo;
-            const uint32_t km = __ballot_sync(0xFFFFFFFFu, keep);
-            const uint32_t tm = __ballot_sync(0xFFFFFFFFu, mem && key > hi);
-            const int first_keep = km ? __ffs(km) - 1 : 32;
-            const int first_term = tm ? __ffs(tm) - 1 : 32;
-            int end = (int)nheavy;
-            if (first_term + 1 < end) end = first_term + 1;
-            if (first_keep + (int)room < end) end = first_keep + (int)room;
-            if (keep && lane < end) {
-                const uint32_t slot = count + (uint32_t)(lane - first_keep);
-                W.key[slot] = key;
-                W.pos[slot] = (uint32_t)(tile0 + off);
-            }
-            if (lane == 0) {
-                const int taken = first_keep < end ? end - first_keep : 0;
-                W.count = count + (uint32_t)taken;
-                if (first_keep < end) W.next_rank = rank0 + (uint64_t)end;
-                if (first_term < end) W.done = 1;
-                if (end >= (int)nheavy) W.tile = t + 1;
-            }
+            if ((uint32_t)lane < nheavy) { S.hkey[swz(lane)] = base + key; S.hoff[lane] = (uint16_t)off; }
+            if (lane == 0) S.hcount = nheavy;
         }
         __syncthreads();
         return;
@@ -645,220 +721,176 @@ __device__ void stream_tile(Win &W, uint32_t t, const uint32_t (&x)[kItems], uin
     uint32_t cnt = 0;
     u128 sum = 0;
 #pragma unroll
+    for (int k = 0; k < kItems; ++k)
+        if (first + k < n && y[k] > light_max) { sum += nq_of(y[k], F32, beta, n32) - Q; ++cnt; }
+    u128 tot;
+    const u128 ex = block_exclusive_scan1(sum, tot, S.scan);
+    uint32_t ctot;
+    uint32_t slot = block_exclusive_scan_u32(cnt, ctot, S.cnt);
+    u128 key = base + ex;
+#pragma unroll
     for (int k = 0; k < kItems; ++k) {
-        if (first + k < n && x[k] > light_max) {
-            sum += times_n(q_of(x[k], F32, beta), n) - Q;
-            ++cnt;
+        if (first + k < n && y[k] > light_max) {
+            key += nq_of(y[k], F32, beta, n32) - Q;
+            S.hkey[swz(slot)] = key;
+            S.hoff[slot] = (uint16_t)(threadIdx.x * kItems + k);
+            ++slot;
         }
     }
-    U2 tot;
-    const U2 ex = block_exclusive_scan2(U2{(u128)cnt, sum}, tot, s_scan);
-    if (threadIdx.x == 0) { s_min[0] = ~0ull; s_min[1] = ~0ull; }
-    __syncthreads();
-    {
-        uint64_t r = rank0 + (uint64_t)ex.a;
-        u128 key = base + ex.b;
-        unsigned long long fk = ~0ull, ft = ~0ull;
-#pragma unroll
-        for (int k = 0; k < kItems; ++k) {
-            if (first + k < n && x[k] > light_max) {
-                key += times_n(q_of(x[k], F32, beta), n) - Q;
-                if (fk == ~0ull && r >= next_rank && key > lo) fk = r;
-                if (ft == ~0ull && key > hi) ft = r;
-                ++r;
-            }
-        }
-        if (fk != ~0ull) atomicMin(&s_min[0], fk);
-        if (ft != ~0ull) atomicMin(&s_min[1], ft);
-    }
-    __syncthreads();
-    const uint64_t r_start = s_min[0], r_term = s_min[1];
-    const uint64_t r_tile_end = rank0 + (uint64_t)tot.a;
-    uint64_t r_end = r_tile_end;
-    if (r_term != ~0ull && r_term + 1 < r_end) r_end = r_term + 1;
-    if (r_start != ~0ull && r_start + room < r_end) r_end = r_start + room;
-    if (r_start != ~0ull) {
-        uint64_t r = rank0 + (uint64_t)ex.a;
-        u128 key = base + ex.b;
-#pragma unroll
-        for (int k = 0; k < kItems; ++k) {
-            if (first + k < n && x[k] > light_max) {
-                key += times_n(q_of(x[k], F32, beta), n) - Q;
-                if (r >= r_start && r < r_end) {
-                    const uint32_t slot = count + (uint32_t)(r - r_start);
-                    W.key[slot] = key;
-                    W.pos[slot] = (uint32_t)(first + k);
-                }
-                ++r;
-            }
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        if (r_start != ~0ull) {
-            W.count = count + (uint32_t)(r_end - r_start);
-            W.next_rank = r_end;
-            if (r_term != ~0ull && r_term < r_end) W.done = 1;
-        }
-        if (r_start == ~0ull || r_end == r_tile_end) W.tile = t + 1;
-    }
+    if (threadIdx.x == 0) S.hcount = ctot;
     __syncthreads();
 }
 
+constexpr int kSweepTiles = 4; // own tiles per block of k_sweep (they share stream tiles)
+
 template <int F32>
-__global__ void __launch_bounds__(kThreads, 2) k_sweep(const uint32_t *__restrict__ w, uint64_t n, int vec,
+__global__ void __launch_bounds__(kThreads, 3) k_sweep(const uint32_t *__restrict__ w, uint64_t n, int vec,
                                                        DevHeader *hdr, const TileSum *__restrict__ incl,
                                                        const Split *__restrict__ split,
                                                        const uint16_t *__restrict__ slist, uint32_t ntiles,
                                                        uint4 *__restrict__ table)
 {
-    __shared__ Win W;
-    __shared__ U2 s_scan[kWarps];
-    __shared__ unsigned long long s_min[2];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SweepSmem &S = *reinterpret_cast<SweepSmem *>(smem_raw);
     if (*(volatile uint32_t *)&hdr->status) return;
-    const uint32_t c = blockIdx.x;
-    const Split sp = split[c];
+    const uint32_t n32 = (uint32_t)n;
     const u128 Q = mk128(hdr->q_lo, hdr->q_hi);
     const uint32_t light_max = hdr->light_max;
     const int beta = hdr->beta;
     const uint32_t shift = hdr->shift;
-    const uint64_t tile0 = (uint64_t)c * kTile;
-    const uint64_t first = tile0 + (uint64_t)threadIdx.x * kItems;
-
-    // own tile and the first two stream tiles, loaded together
-    uint32_t x[kItems], xa[kItems], xb[kItems];
-    load_items(w, n, vec, first, x);
-    const uint32_t s0 = sp.hb;
-    if (s0 < ntiles) load_items(w, n, vec, (uint64_t)s0 * kTile + (uint64_t)threadIdx.x * kItems, xa);
-    if (s0 + 1 < ntiles) load_items(w, n, vec, (uint64_t)(s0 + 1) * kTile + (uint64_t)threadIdx.x * kItems, xb);
-
-    const Prefix pc = prefix_at(incl, c, n);
-    const u128 D_start = key_D(pc, n, Q);
-    uint32_t lmask = 0;
-    u128 def = 0;
-#pragma unroll
-    for (int k = 0; k < kItems; ++k) {
-        if (first + k < n && x[k] <= light_max) {
-            lmask |= 1u << k;
-            def += Q - times_n(q_of(x[k], F32, beta), n);
-        }
-    }
-    U2 tot;
-    const U2 ex = block_exclusive_scan2(U2{def, (u128)0}, tot, s_scan);
-    const u128 K0 = D_start + ex.a; // key of my first light
-    const u128 K1 = K0 + def;       // key after my last light
-    const u128 D_end = D_start + tot.a;
-
-    uint64_t rthr[kItems];
-    uint32_t ralias[kItems];
-#pragma unroll
-    for (int k = 0; k < kItems; ++k) { rthr[k] = 0; ralias[k] = 0; }
-    uint32_t pend = lmask;
+    const uint32_t c_first = blockIdx.x * kSweepTiles;
+    const uint32_t c_last = min(c_first + kSweepTiles, ntiles);
     bool bad = false;
-    if (threadIdx.x == 0) {
-        W.count = 0;
-        W.done = 0;
-        W.tile = s0;
-        W.next_rank = 0;
-    }
-    __syncthreads();
-    if (!__syncthreads_or(lmask != 0)) return; // no lights: nothing is packed here
 
-    for (int round = 0;; ++round) {
-        // ---- fill the window
-        if (threadIdx.x == 0) W.count = 0;
-        __syncthreads();
-        for (;;) {
-            if (W.done || W.count >= (uint32_t)kTile) break;
-            const uint32_t t = W.tile;
-            if (t >= ntiles) {
-                if (threadIdx.x == 0) {
-                    W.key[W.count] = ~(u128)0;
-                    W.pos[W.count] = kNone;
-                    W.count += 1;
-                    W.done = 1;
-                }
-                __syncthreads();
-                break;
-            }
-            if (t == s0) stream_tile<F32>(W, t, xa, n, incl, slist, w, Q, light_max, beta, D_start, D_end, s_scan, s_min);
-            else if (t == s0 + 1) stream_tile<F32>(W, t, xb, n, incl, slist, w, Q, light_max, beta, D_start, D_end, s_scan, s_min);
-            else {
-                uint32_t y[kItems];
-                load_items(w, n, vec, (uint64_t)t * kTile + (uint64_t)threadIdx.x * kItems, y);
-                stream_tile<F32>(W, t, y, n, incl, slist, w, Q, light_max, beta, D_start, D_end, s_scan, s_min);
+    uint32_t x[kItems], y[kItems];
+    load_items(w, n, vec, (uint64_t)c_first * kTile + (uint64_t)threadIdx.x * kItems, x);
+    uint32_t s = split[c_first].hb;   // current stream tile
+    uint32_t s_loaded = kNone;        // stream tile whose heavies are in S.hkey
+    uint32_t y_tile = kNone;          // stream tile whose words are in y
+    if (s < ntiles) { load_items(w, n, vec, (uint64_t)s * kTile + (uint64_t)threadIdx.x * kItems, y); y_tile = s; }
+
+    for (uint32_t c = c_first; c < c_last; ++c) {
+        const uint64_t tile0 = (uint64_t)c * kTile;
+        // own lights: keys D (exclusive prefix of the deficits Q - n*q) and offsets
+        uint32_t lmask = 0;
+        u128 def = 0;
+#pragma unroll
+        for (int k = 0; k < kItems; ++k) {
+            if (tile0 + threadIdx.x * kItems + k < n && x[k] <= light_max) {
+                lmask |= 1u << k;
+                def += Q - nq_of(x[k], F32, beta, n32);
             }
         }
-        const uint32_t cnt = W.count;
-        const bool complete = W.done != 0;
-        // ---- my lights: alias = first heavy with E > D
+        const Prefix pc = prefix_at(incl, c, n);
+        const u128 D_start = key_D(pc, n, Q);
+        u128 dtot;
+        const u128 K0 = D_start + block_exclusive_scan1(def, dtot, S.scan); // syncs: S.okey is free
+        uint32_t nl;
+        uint32_t lslot = block_exclusive_scan_u32((uint32_t)__popc(lmask), nl, S.cnt);
+        const u128 D_end = D_start + dtot;
         {
             u128 kl = K0;
-            int yi = -1;
 #pragma unroll
             for (int k = 0; k < kItems; ++k) {
                 if ((lmask >> k) & 1u) {
-                    const u128 nq = times_n(q_of(x[k], F32, beta), n);
-                    const u128 key = kl;
-                    kl += Q - nq;
-                    if ((pend >> k) & 1u) {
-                        if (yi < 0) yi = (int)upper_bound_keys(W.key, cnt, key);
-                        else while ((uint32_t)yi < cnt && W.key[yi] <= key) ++yi;
-                        if ((uint32_t)yi >= cnt) break;
-                        const uint32_t al = W.pos[yi];
-                        if (al == kNone && nq != Q) bad = true;
-                        rthr[k] = lo64(nq >> shift);
-                        ralias[k] = (al == kNone || nq == Q) ? (uint32_t)(first + k) : al;
-                        pend &= ~(1u << k);
-                    }
+                    S.okey[swz(lslot)] = kl;
+                    S.ooff[lslot] = (uint16_t)(threadIdx.x * kItems + k);
+                    ++lslot;
+                    kl += Q - nq_of(x[k], F32, beta, n32);
                 }
             }
         }
-        // ---- heavies with E in (K0, K1] among entries [0, cnt - 1)
-        if (K1 > K0) {
-            const uint32_t lim = cnt - 1;
-            uint32_t ylo = upper_bound_keys(W.key, lim, K0);
-            const uint32_t yhi = upper_bound_keys(W.key, lim, K1);
-            u128 kl = K0;
-            int k = 0;
-            for (uint32_t yv = ylo; yv < yhi; ++yv) {
-                const u128 e = W.key[yv];
-                // advance to the first of my lights with key >= e (else K1)
-                while (k < kItems) {
-                    if ((lmask >> k) & 1u) {
-                        if (kl >= e) break;
-                        kl += Q - times_n(q_of(x[k], F32, beta), n);
-                    }
-                    ++k;
+        // prefetch the next own tile
+        if (c + 1 < c_last) load_items(w, n, vec, (uint64_t)(c + 1) * kTile + (uint64_t)threadIdx.x * kItems, x);
+        if (nl == 0) continue; // no lights: nothing is packed for this tile
+        uint32_t al = 0; // own lights resolved so far
+        for (;;) {
+            if (s >= ntiles) {
+                // no heavy item left: the remaining own lights are exactly full
+                __syncthreads();
+                for (uint32_t i = al + threadIdx.x; i < nl; i += kThreads) {
+                    const u128 dn = (i + 1 < nl) ? S.okey[swz(i + 1)] : D_end;
+                    const u128 nq = Q - (dn - S.okey[swz(i)]);
+                    if (nq != Q) bad = true;
+                    const uint32_t me = (uint32_t)(tile0 + S.ooff[i]);
+                    const uint64_t thr = lo64(nq >> shift);
+                    table[me] = make_uint4((uint32_t)thr, (uint32_t)(thr >> 32), me, 0u);
                 }
-                const u128 dnext = (k < kItems) ? kl : K1;
-                const u128 gap = dnext - e;
-                if (gap >= Q) bad = true;
-                const u128 bw = Q - gap;
-                const uint32_t me = W.pos[yv], nx = W.pos[yv + 1];
-                if (nx == kNone && bw != Q) bad = true;
-                const uint32_t al = (nx == kNone || bw == Q) ? me : nx;
-                const uint64_t thr = lo64(bw >> shift);
-                table[me] = make_uint4((uint32_t)thr, (uint32_t)(thr >> 32), al, 0u);
+                break;
             }
+            if (s != s_loaded) {
+                const uint32_t nheavy = tilesum_ldcg(incl + s).nheavy;
+                if (nheavy == 0) { ++s; continue; }
+                if (y_tile != s && nheavy > (uint32_t)kSparse) {
+                    load_items(w, n, vec, (uint64_t)s * kTile + (uint64_t)threadIdx.x * kItems, y);
+                    y_tile = s;
+                }
+                __syncthreads(); // previous window consumed
+                load_heavies<F32>(S, s, y, nheavy, n, n32, incl, slist, w, Q, light_max, beta);
+                s_loaded = s;
+                // prefetch the following stream tile
+                if (s + 1 < ntiles) {
+                    load_items(w, n, vec, (uint64_t)(s + 1) * kTile + (uint64_t)threadIdx.x * kItems, y);
+                    y_tile = s + 1;
+                }
+            }
+            const uint32_t hc = S.hcount;
+            __syncthreads(); // own keys and window complete
+            if (threadIdx.x < 3) {
+                uint32_t r;
+                if (threadIdx.x == 0) r = lb_keys(S.okey, al, nl, S.hkey[swz(hc - 1)]); // lights answered here
+                else if (threadIdx.x == 1) r = ub_keys(S.hkey, 0, hc, D_start);         // heavies packed here:
+                else r = ub_keys(S.hkey, 0, hc, D_end);                                // E in (D_start, D_end]
+                S.rng[1 + threadIdx.x] = r;
+            }
+            __syncthreads();
+            const uint32_t a0 = al, a1 = S.rng[1], b0 = S.rng[2], b1 = S.rng[3];
+            const uint32_t na = a1 - a0, nb = b1 > b0 ? b1 - b0 : 0, M = na + nb;
+            const uint32_t per = (M + kThreads - 1) / kThreads;
+            const uint64_t sbase = (uint64_t)s * kTile;
+            const uint32_t d0 = threadIdx.x * per;
+            if (d0 < M) {
+                // co-rank: number of heavies among the first d0 merged elements
+                uint32_t lo = d0 > na ? d0 - na : 0, hi = d0 < nb ? d0 : nb;
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi + 1) >> 1; // is heavy b0+mid-1 before light a0+d0-mid?
+                    if (S.hkey[swz(b0 + mid - 1)] <= S.okey[swz(a0 + d0 - mid)]) lo = mid; else hi = mid - 1;
+                }
+                uint32_t j = b0 + lo, i = a0 + (d0 - lo);
+                const uint32_t steps = min(per, M - d0);
+                for (uint32_t st = 0; st < steps; ++st) {
+                    const bool heavy_next = (j < b1) && (i >= a1 || S.hkey[swz(j)] <= S.okey[swz(i)]);
+                    if (heavy_next) {
+                        const u128 e = S.hkey[swz(j)];
+                        const u128 dn = (i < nl) ? S.okey[swz(i)] : D_end;
+                        const u128 gap = dn - e;
+                        if (gap >= Q) bad = true;
+                        const u128 bw = Q - gap;
+                        const uint32_t me = (uint32_t)(sbase + S.hoff[j]);
+                        const uint32_t nx = (j + 1 < hc) ? (uint32_t)(sbase + S.hoff[j + 1]) : split[s].next_heavy;
+                        if (nx == kNone && bw != Q) bad = true;
+                        const uint32_t alias = (nx == kNone || bw == Q) ? me : nx;
+                        const uint64_t thr = lo64(bw >> shift);
+                        table[me] = make_uint4((uint32_t)thr, (uint32_t)(thr >> 32), alias, 0u);
+                        ++j;
+                    } else {
+                        const u128 d = S.okey[swz(i)];
+                        const u128 dn = (i + 1 < nl) ? S.okey[swz(i + 1)] : D_end;
+                        const u128 nq = Q - (dn - d);
+                        const uint32_t me = (uint32_t)(tile0 + S.ooff[i]);
+                        const uint32_t alias = (nq == Q) ? me : (uint32_t)(sbase + S.hoff[j]); // j < hc: current heavy
+                        const uint64_t thr = lo64(nq >> shift);
+                        table[me] = make_uint4((uint32_t)thr, (uint32_t)(thr >> 32), alias, 0u);
+                        ++i;
+                    }
+                }
+            }
+            al = a1;
+            if (b1 < hc) break; // the first heavy past D_end is in this tile: this own tile is done
+            ++s;
         }
-        if (complete) break;
-        // the last entry waits for its successor: restart the stream there
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            W.next_rank = W.next_rank - 1;
-            const uint32_t lastpos = W.pos[cnt - 1];
-            W.tile = lastpos / (uint32_t)kTile;
-        }
-        __syncthreads();
     }
-    if (pend) bad = true;
     if (bad) set_status(hdr, kEInternal);
-    // ---- write my lights' buckets
-#pragma unroll
-    for (int k = 0; k < kItems; ++k)
-        if ((lmask >> k) & 1u)
-            table[first + k] = make_uint4((uint32_t)rthr[k], (uint32_t)(rthr[k] >> 32), ralias[k], 0u);
 }
 
 // ----------------------------------------------------------- k_sample
