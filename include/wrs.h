@@ -178,6 +178,53 @@ uint32_t wrs_set_wait_limit(uint32_t polls);
  * tests only. */
 void wrs_debug_skip_publish(int64_t tile);
 
+/*
+ * Build without allocating (no counterpart in the paper).
+ *
+ * For callers that cannot call cudaMalloc -- code running inside a CUDA graph
+ * being captured or replayed, real-time or embedded processes whose memory is
+ * fixed at start-up, host frameworks that own all device memory through their
+ * own pool -- this entry point builds the same table as wrs_table_build
+ * (bucket for bucket) into memory the caller owns, and keeps its scratch in
+ * one static device array inside the library, sized for WRS_NOALLOC_MAX_N
+ * weights (about 0.5 MB; every GPU that loads the library holds it until the
+ * process exits).  It allocates nothing and calls no allocating routine.
+ *
+ *   d_weights  n words of dtype, device memory, 4-byte aligned, read only
+ *   d_buckets  output: n wrs_bucket, device memory, 16-byte aligned
+ *   d_header   output: one wrs_device_header (WRS_DEVICE_HEADER_BYTES),
+ *              device memory, 16-byte aligned; its status word reports
+ *              device-detected errors as in wrs_table_status()
+ *   n          1 .. WRS_NOALLOC_MAX_N; larger n returns WRS_EINVAL at once
+ *              (use wrs_table_create/wrs_table_build instead)
+ *
+ * Asynchronous on `stream`.  The first call on a device looks up the static
+ * array's device address (cudaGetSymbolAddress) and sets the sweep kernel's
+ * shared-memory attribute; make that first call before any stream capture.
+ * All calls share the one array: two calls whose work overlaps on the GPU
+ * (different streams, or several host threads) race and corrupt each
+ * other's results, so order them (one stream, or events).  The array keeps
+ * the last call's contents; nothing in it needs to start at zero. */
+#define WRS_NOALLOC_MAX_N (1ull << 22)
+#define WRS_DEVICE_HEADER_BYTES 128
+
+typedef struct {
+    uint32_t status;      /* wrs_status of the build */
+    uint32_t reserved0;
+    int32_t beta;         /* exponent of the integer unit */
+    uint32_t shift;       /* thr = bw >> shift */
+    uint64_t q_lo, q_hi;  /* Q */
+    uint64_t qp;          /* Q >> shift: the sampler's coin denominator */
+    uint32_t light_max;   /* light iff raw word <= light_max */
+    uint32_t reserved1;
+    uint64_t n;
+    uint64_t n_light;
+    uint64_t reserved2[8];
+} wrs_device_header;
+
+wrs_status wrs_build_noalloc(const void *d_weights, uint64_t n, wrs_dtype dtype,
+                             void *d_buckets, void *d_header, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

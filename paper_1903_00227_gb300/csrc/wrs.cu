@@ -419,3 +419,118 @@ void wrs_debug_skip_publish(int64_t tile)
 }
 
 } // extern "C"
+
+// ---------------------------------------------------------------------------
+// Build without any allocation (wrs_build_noalloc).
+//
+// Some callers cannot call cudaMalloc: code that runs inside a CUDA graph
+// being captured or replayed, a real-time or embedded process whose memory
+// budget is fixed at start-up, or a host framework that owns all device
+// memory through its own pool.  For them, the build's scratch (per-block
+// partial sums, tile sums and prefixes, look-back flags, split results,
+// sparse member lists) lives in one file-scope device array sized for
+// WRS_NOALLOC_MAX_N weights; the caller passes the weights, the output
+// buckets and the output header.  Every GPU that loads the library holds
+// this array until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr uint64_t kNaMaxN = WRS_NOALLOC_MAX_N;
+constexpr uint32_t kNaTiles = (uint32_t)((kNaMaxN + kTile - 1) / kTile);
+constexpr uint32_t kNaChunks = (kNaTiles + kScanChunk - 1) / kScanChunk;
+constexpr uint64_t na_up(uint64_t x) { return (x + 255) / 256 * 256; }
+constexpr uint64_t kNaPart = 0;
+constexpr uint64_t kNaAgg = kNaPart + na_up(kMaxParts * sizeof(Partial));
+constexpr uint64_t kNaIncl = kNaAgg + na_up((uint64_t)kNaTiles * sizeof(TileSum));
+constexpr uint64_t kNaCagg = kNaIncl + na_up((uint64_t)kNaTiles * sizeof(TileSum));
+constexpr uint64_t kNaCincl = kNaCagg + na_up((uint64_t)kNaChunks * sizeof(TileSum));
+constexpr uint64_t kNaFlags = kNaCincl + na_up((uint64_t)kNaChunks * sizeof(TileSum));
+constexpr uint64_t kNaSplit = kNaFlags + na_up((uint64_t)kNaChunks * sizeof(uint32_t));
+constexpr uint64_t kNaSlist = kNaSplit + na_up((uint64_t)kNaTiles * sizeof(Split));
+constexpr uint64_t kNaBytes = kNaSlist + na_up((uint64_t)kNaTiles * kSparse * sizeof(uint16_t));
+
+// Zero at module load; the look-back flags carry a generation number, so no
+// call has to clear them.
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+struct NoallocDevice {
+    unsigned char *scratch; // device address of g_noalloc_scratch on this device
+    uint32_t epoch;
+    bool ready;
+};
+NoallocDevice g_noalloc[64];
+
+static_assert(sizeof(DevHeader) <= WRS_DEVICE_HEADER_BYTES, "device header does not fit");
+static_assert(offsetof(DevHeader, status) == offsetof(wrs_device_header, status), "layout");
+static_assert(offsetof(DevHeader, beta) == offsetof(wrs_device_header, beta), "layout");
+static_assert(offsetof(DevHeader, shift) == offsetof(wrs_device_header, shift), "layout");
+static_assert(offsetof(DevHeader, q_lo) == offsetof(wrs_device_header, q_lo), "layout");
+static_assert(offsetof(DevHeader, q_hi) == offsetof(wrs_device_header, q_hi), "layout");
+static_assert(offsetof(DevHeader, qp) == offsetof(wrs_device_header, qp), "layout");
+static_assert(offsetof(DevHeader, light_max) == offsetof(wrs_device_header, light_max), "layout");
+static_assert(offsetof(DevHeader, n) == offsetof(wrs_device_header, n), "layout");
+static_assert(offsetof(DevHeader, n_light) == offsetof(wrs_device_header, n_light), "layout");
+static_assert(sizeof(wrs_device_header) == WRS_DEVICE_HEADER_BYTES, "layout");
+
+} // namespace
+
+extern "C" wrs_status wrs_build_noalloc(const void *d_weights, uint64_t n, wrs_dtype dtype, void *d_buckets,
+                                        void *d_header, void *stream)
+{
+    if (!d_weights || !d_buckets || !d_header || n == 0) return WRS_EINVAL;
+    if (n > kNaMaxN) return WRS_EINVAL; // beyond the static scratch: use wrs_table_create/wrs_table_build
+    if (dtype != WRS_U32 && dtype != WRS_F32) return WRS_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_weights) % 4) != 0) return WRS_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_buckets) % 16) != 0 || (reinterpret_cast<uintptr_t>(d_header) % 16) != 0)
+        return WRS_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return WRS_EDEVICE;
+    NoallocDevice &D = g_noalloc[dev];
+    if (!D.ready) {
+        // once per device, with that device current: the array's device address
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return WRS_EDEVICE;
+        const wrs_status st = set_kernel_attributes();
+        if (st != WRS_OK) return st;
+        D.scratch = static_cast<unsigned char *>(ptr);
+        D.epoch = 0;
+        D.ready = true;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const uint32_t *w = static_cast<const uint32_t *>(d_weights);
+    const int vec = (reinterpret_cast<uintptr_t>(w) % 16) == 0;
+    const uint32_t ntiles = (uint32_t)((n + kTile - 1) / kTile);
+    const uint32_t nchunks = (ntiles + kScanChunk - 1) / kScanChunk;
+    const uint32_t f32 = dtype == WRS_F32;
+    DevHeader *hdr = static_cast<DevHeader *>(d_header);
+    uint4 *buckets = static_cast<uint4 *>(d_buckets);
+    Partial *part = reinterpret_cast<Partial *>(D.scratch + kNaPart);
+    TileSum *agg = reinterpret_cast<TileSum *>(D.scratch + kNaAgg);
+    TileSum *incl = reinterpret_cast<TileSum *>(D.scratch + kNaIncl);
+    TileSum *cagg = reinterpret_cast<TileSum *>(D.scratch + kNaCagg);
+    TileSum *cincl = reinterpret_cast<TileSum *>(D.scratch + kNaCincl);
+    uint32_t *flags = reinterpret_cast<uint32_t *>(D.scratch + kNaFlags);
+    Split *split = reinterpret_cast<Split *>(D.scratch + kNaSplit);
+    uint16_t *slist = reinterpret_cast<uint16_t *>(D.scratch + kNaSlist);
+
+    uint64_t want = (n + (uint64_t)kThreads * 16 - 1) / ((uint64_t)kThreads * 16);
+    uint32_t nparts = (uint32_t)(want < 1 ? 1 : (want > kMaxParts ? kMaxParts : want));
+    const uint32_t blocks_cap = (uint32_t)sm_count() * 8;
+    if (nparts > blocks_cap) nparts = blocks_cap;
+    uint32_t cls_blocks = blocks_cap < ntiles ? blocks_cap : ntiles;
+    D.epoch = D.epoch + 1;
+    if (D.epoch >= (1u << 30)) D.epoch = 1;
+
+    if (f32) k_stats<1><<<nparts, kThreads, 0, s>>>(w, n, vec, part);
+    else k_stats<0><<<nparts, kThreads, 0, s>>>(w, n, vec, part);
+    k_stats_combine<<<1, kThreads, 0, s>>>(part, nparts, n, f32, hdr);
+    if (f32) k_classify<1><<<cls_blocks, kThreads, 0, s>>>(w, n, vec, hdr, agg, slist, ntiles);
+    else k_classify<0><<<cls_blocks, kThreads, 0, s>>>(w, n, vec, hdr, agg, slist, ntiles);
+    k_tilescan<<<nchunks, kThreads, 0, s>>>(hdr, agg, cagg, cincl, incl, flags, ntiles, D.epoch,
+                                            g_wait_limit.load(), kNone);
+    k_split<<<(ntiles + kThreads - 1) / kThreads, kThreads, 0, s>>>(incl, ntiles, n, hdr, split);
+    const uint32_t sweep_blocks = (ntiles + kSweepTiles - 1) / kSweepTiles;
+    if (f32) k_sweep<1><<<sweep_blocks, kThreads, sizeof(SweepSmem), s>>>(w, n, vec, hdr, incl, split, slist, ntiles, buckets);
+    else k_sweep<0><<<sweep_blocks, kThreads, sizeof(SweepSmem), s>>>(w, n, vec, hdr, incl, split, slist, ntiles, buckets);
+    return launch_err();
+}

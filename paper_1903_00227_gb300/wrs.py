@@ -72,6 +72,7 @@ _sig = {
     "wrs_status_str": ([_I], ctypes.c_char_p),
     "wrs_set_wait_limit": ([ctypes.c_uint32], ctypes.c_uint32),
     "wrs_debug_skip_publish": ([ctypes.c_int64], None),
+    "wrs_build_noalloc": ([_P, _U64, _I, _P, _P, _P], _I),
 }
 for _name, (_args, _res) in _sig.items():
     _f = getattr(_lib, _name)
@@ -170,6 +171,16 @@ def set_wait_limit(polls: int) -> int:
 
 def debug_skip_publish(tile: int) -> None:
     _lib.wrs_debug_skip_publish(tile)
+
+
+NOALLOC_MAX_N = 1 << 22
+DEVICE_HEADER_BYTES = 128
+
+
+def build_noalloc(d_weights: int, n: int, dtype: int, d_buckets: int, d_header: int, stream: int = 0) -> int:
+    """wrs_build_noalloc: build into caller-owned buckets and header using the
+    library's static scratch (no allocation)."""
+    return _lib.wrs_build_noalloc(d_weights, n, dtype, d_buckets, d_header, stream)
 
 
 # --- convenience wrapper over torch tensors --------------------------------
