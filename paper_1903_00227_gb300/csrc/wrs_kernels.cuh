@@ -660,8 +660,8 @@ __device__ __forceinline__ uint32_t swz(uint32_t j) { return j ^ ((j >> 3) & 7u)
 struct SweepSmem {
     u128 okey[kTile];     // keys D of the own lights, in order (swizzled)
     u128 hkey[kTile];     // keys E of the current stream tile's heavies (swizzled)
-    uint16_t ooff[kTile]; // offsets of the own lights in the tile
-    uint16_t hoff[kTile]; // offsets of the stream tile's heavies
+    uint16_t ooff[kTile];   // offsets of the own lights in the tile
+    uint16_t hoff[kTile];   // offsets of the stream tile's heavies
     u128 scan[kWarps];
     uint32_t cnt[kWarps];
     uint32_t hcount;
@@ -718,23 +718,34 @@ __device__ __forceinline__ void load_heavies(SweepSmem &S, uint32_t t, const uin
         return;
     }
     const uint64_t first = tile0 + (uint64_t)threadIdx.x * kItems;
-    uint32_t cnt = 0;
-    u128 sum = 0;
+    uint32_t hm = 0;
 #pragma unroll
     for (int k = 0; k < kItems; ++k)
-        if (first + k < n && y[k] > light_max) { sum += nq_of(y[k], F32, beta, n32) - Q; ++cnt; }
-    u128 tot;
-    const u128 ex = block_exclusive_scan1(sum, tot, S.scan);
+        if (first + k < n && y[k] > light_max) hm |= 1u << k;
     uint32_t ctot;
-    uint32_t slot = block_exclusive_scan_u32(cnt, ctot, S.cnt);
-    u128 key = base + ex;
+    const uint32_t slot0 = block_exclusive_scan_u32((uint32_t)__popc(hm), ctot, S.cnt);
+    // excesses n*q - Q into the key slots, then an in-place prefix
+    u128 sum = 0;
+    {
+        uint32_t slot = slot0;
 #pragma unroll
-    for (int k = 0; k < kItems; ++k) {
-        if (first + k < n && y[k] > light_max) {
-            key += nq_of(y[k], F32, beta, n32) - Q;
-            S.hkey[swz(slot)] = key;
-            S.hoff[slot] = (uint16_t)(threadIdx.x * kItems + k);
-            ++slot;
+        for (int k = 0; k < kItems; ++k) {
+            if ((hm >> k) & 1u) {
+                const u128 e = nq_of(y[k], F32, beta, n32) - Q;
+                S.hkey[swz(slot)] = e;
+                S.hoff[slot] = (uint16_t)(threadIdx.x * kItems + k);
+                sum += e;
+                ++slot;
+            }
+        }
+    }
+    u128 tot;
+    u128 key = base + block_exclusive_scan1(sum, tot, S.scan);
+    {
+        const uint32_t cnt = (uint32_t)__popc(hm);
+        for (uint32_t j = 0; j < cnt; ++j) {
+            key += S.hkey[swz(slot0 + j)];
+            S.hkey[swz(slot0 + j)] = key;
         }
     }
     if (threadIdx.x == 0) S.hcount = ctot;
@@ -771,42 +782,48 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep(const uint32_t *__restric
 
     for (uint32_t c = c_first; c < c_last; ++c) {
         const uint64_t tile0 = (uint64_t)c * kTile;
-        // own lights: keys D (exclusive prefix of the deficits Q - n*q) and offsets
+        const uint64_t first = tile0 + (uint64_t)threadIdx.x * kItems;
+        // own lights: deficits Q - n*q, thresholds n*q >> shift, full lights
         uint32_t lmask = 0;
-        u128 def = 0;
 #pragma unroll
-        for (int k = 0; k < kItems; ++k) {
-            if (tile0 + threadIdx.x * kItems + k < n && x[k] <= light_max) {
-                lmask |= 1u << k;
-                def += Q - nq_of(x[k], F32, beta, n32);
+        for (int k = 0; k < kItems; ++k)
+            if (first + k < n && x[k] <= light_max) lmask |= 1u << k;
+        uint32_t nl;
+        const uint32_t lslot0 = block_exclusive_scan_u32((uint32_t)__popc(lmask), nl, S.cnt); // syncs: okey free
+        u128 def = 0;
+        {
+            uint32_t slot = lslot0;
+#pragma unroll
+            for (int k = 0; k < kItems; ++k) {
+                if ((lmask >> k) & 1u) {
+                    const u128 d = Q - nq_of(x[k], F32, beta, n32);
+                    S.okey[swz(slot)] = d;
+                    S.ooff[slot] = (uint16_t)(threadIdx.x * kItems + k);
+                    def += d;
+                    ++slot;
+                }
             }
         }
         const Prefix pc = prefix_at(incl, c, n);
         const u128 D_start = key_D(pc, n, Q);
         u128 dtot;
-        const u128 K0 = D_start + block_exclusive_scan1(def, dtot, S.scan); // syncs: S.okey is free
-        uint32_t nl;
-        uint32_t lslot = block_exclusive_scan_u32((uint32_t)__popc(lmask), nl, S.cnt);
-        const u128 D_end = D_start + dtot;
         {
-            u128 kl = K0;
-#pragma unroll
-            for (int k = 0; k < kItems; ++k) {
-                if ((lmask >> k) & 1u) {
-                    S.okey[swz(lslot)] = kl;
-                    S.ooff[lslot] = (uint16_t)(threadIdx.x * kItems + k);
-                    ++lslot;
-                    kl += Q - nq_of(x[k], F32, beta, n32);
-                }
+            u128 kl = D_start + block_exclusive_scan1(def, dtot, S.scan);
+            const uint32_t cnt = (uint32_t)__popc(lmask);
+            for (uint32_t j = 0; j < cnt; ++j) { // deficits -> exclusive keys, in place
+                const u128 d = S.okey[swz(lslot0 + j)];
+                S.okey[swz(lslot0 + j)] = kl;
+                kl += d;
             }
         }
+        const u128 D_end = D_start + dtot;
         // prefetch the next own tile
         if (c + 1 < c_last) load_items(w, n, vec, (uint64_t)(c + 1) * kTile + (uint64_t)threadIdx.x * kItems, x);
         if (nl == 0) continue; // no lights: nothing is packed for this tile
         uint32_t al = 0; // own lights resolved so far
         for (;;) {
             if (s >= ntiles) {
-                // no heavy item left: the remaining own lights are exactly full
+                // no heavy item left: the remaining own lights must be exactly full
                 __syncthreads();
                 for (uint32_t i = al + threadIdx.x; i < nl; i += kThreads) {
                     const u128 dn = (i + 1 < nl) ? S.okey[swz(i + 1)] : D_end;
@@ -828,8 +845,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep(const uint32_t *__restric
                 __syncthreads(); // previous window consumed
                 load_heavies<F32>(S, s, y, nheavy, n, n32, incl, slist, w, Q, light_max, beta);
                 s_loaded = s;
-                // prefetch the following stream tile
-                if (s + 1 < ntiles) {
+                if (s + 1 < ntiles) { // prefetch the following stream tile
                     load_items(w, n, vec, (uint64_t)(s + 1) * kTile + (uint64_t)threadIdx.x * kItems, y);
                     y_tile = s + 1;
                 }
@@ -858,12 +874,12 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep(const uint32_t *__restric
                 }
                 uint32_t j = b0 + lo, i = a0 + (d0 - lo);
                 const uint32_t steps = min(per, M - d0);
+                u128 ej = j < b1 ? S.hkey[swz(j)] : (u128)0;
+                u128 di = i < nl ? S.okey[swz(i)] : D_end; // key of light i (D_end past the last)
                 for (uint32_t st = 0; st < steps; ++st) {
-                    const bool heavy_next = (j < b1) && (i >= a1 || S.hkey[swz(j)] <= S.okey[swz(i)]);
+                    const bool heavy_next = (j < b1) && (i >= a1 || ej <= di);
                     if (heavy_next) {
-                        const u128 e = S.hkey[swz(j)];
-                        const u128 dn = (i < nl) ? S.okey[swz(i)] : D_end;
-                        const u128 gap = dn - e;
+                        const u128 gap = di - ej;
                         if (gap >= Q) bad = true;
                         const u128 bw = Q - gap;
                         const uint32_t me = (uint32_t)(sbase + S.hoff[j]);
@@ -873,15 +889,16 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep(const uint32_t *__restric
                         const uint64_t thr = lo64(bw >> shift);
                         table[me] = make_uint4((uint32_t)thr, (uint32_t)(thr >> 32), alias, 0u);
                         ++j;
-                    } else {
-                        const u128 d = S.okey[swz(i)];
+                        if (j < b1) ej = S.hkey[swz(j)];
+                    } else { // light i; j < hc: heavy j is its current heavy
                         const u128 dn = (i + 1 < nl) ? S.okey[swz(i + 1)] : D_end;
-                        const u128 nq = Q - (dn - d);
+                        const u128 nq = Q - (dn - di);
                         const uint32_t me = (uint32_t)(tile0 + S.ooff[i]);
-                        const uint32_t alias = (nq == Q) ? me : (uint32_t)(sbase + S.hoff[j]); // j < hc: current heavy
+                        const uint32_t alias = (nq == Q) ? me : (uint32_t)(sbase + S.hoff[j]);
                         const uint64_t thr = lo64(nq >> shift);
                         table[me] = make_uint4((uint32_t)thr, (uint32_t)(thr >> 32), alias, 0u);
                         ++i;
+                        di = dn;
                     }
                 }
             }
