@@ -152,6 +152,25 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def reduce_max(values, device):
+    """Max over ranks of a list of floats (identity on one rank)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_rates(world: int, steps: int, n: int, k: int, t_build_ms: float, t_sample_ms: float):
+    """Whole-job throughput of `world` replicas that each built `steps` tables
+    of n weights and drew `steps` x k samples, timed by the slowest rank:
+    (Gweights/s, Gsamples/s)."""
+    return (world * steps * n / (t_build_ms * 1e-3) / 1e9, world * steps * k / (t_sample_ms * 1e-3) / 1e9)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -298,13 +317,9 @@ def run_ours(args, names):
     t_build = sum(r[1] for r in recs)
     t_sample = sum(r[2] for r in recs)
     step_ms = [r[1] + r[2] for r in recs]
-    if ws > 1:
-        tt = torch.tensor([t_build, t_sample, sum(step_ms)], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_build, t_sample, _ = tt.tolist()
+    t_build, t_sample = reduce_max([t_build, t_sample], "cuda")
     K = args.steps
-    value = ws * K * n / (t_build * 1e-3) / 1e9
-    sample_rate = ws * K * k / (t_sample * 1e-3) / 1e9
+    value, sample_rate = job_rates(ws, K, n, k, t_build, t_sample)
 
     # per-kernel mean durations (events on the launching stream)
     stage_ms = {s: statistics.mean(r[3][s] for r in recs) for s in wrs.STAGES}
@@ -332,6 +347,24 @@ def run_ours(args, names):
                               "build_frac": BUILD_BYTES_PER_WEIGHT * n / (bm * 1e-3) / 1e9 / peak,
                               "sample_ms": sm_, "sample_gsamples_s": k / (sm_ * 1e-3) / 1e9}
 
+    # practical ceiling of random 16-B bucket gathers from a table this size
+    gather = None
+    if k > 0:
+        gt = []
+        for i in range(4):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            WL.random_gather(wrs.table_buckets(table.handle), n, k, 77 + i, out.data_ptr(), sh)
+            e1.record(stream)
+            e1.synchronize()
+            if i:
+                gt.append(e0.elapsed_time(e1))
+        gms = statistics.mean(gt)
+        gather = {"gsamples_s": k / (gms * 1e-3) / 1e9, "ms": gms,
+                  "sampler_fraction": gms / (t_sample / K),
+                  "note": "random 16-B gathers from the same table with no RNG or coin: the random-access ceiling"}
+
     # end to end through the C ABI with host buffers (copies inside the timed region)
     e2e = None
     if args.e2e_steps > 0:
@@ -353,11 +386,7 @@ def run_ours(args, names):
             e1.synchronize()
             if i > 0:  # first call allocates the staging buffers
                 times.append(e0.elapsed_time(e1))
-        t_e2e = statistics.mean(times)
-        if ws > 1:
-            tt = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            t_e2e = tt.item()
+        t_e2e = reduce_max([statistics.mean(times)], "cuda")[0]
         e2e = {"value": ws * n / (t_e2e * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": 4 * n,
                "d2h_bytes_per_step": 4 * k, "ms_per_step": t_e2e,
                "note": "wrs_table_build_host (H2D of the weights) + wrs_sample_host (D2H of the samples)"}
@@ -373,7 +402,8 @@ def run_ours(args, names):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": args.warmup,
             "ms_per_step": statistics.mean(step_ms), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u128", "data": "synthetic", "config": config(args, names),
-            "sample": {"value": sample_rate, "unit": "Gsamples/s", "ms": t_sample / K},
+            "sample": {"value": sample_rate, "unit": "Gsamples/s", "ms": t_sample / K,
+                       "random_gather_ceiling": gather},
             "p99_ms": p99,
             "roofline": roofline,
             "roofline_build": {"bound": "hbm", "achieved": ach_build, "peak": peak, "unit": "GB/s",

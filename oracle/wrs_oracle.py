@@ -81,6 +81,32 @@ def lib():
     return _lib
 
 
+class use_library:
+    """Run the oracle functions of this module against another build of
+    wrs_oracle.c (used by the tests that plant mistakes in the oracle)."""
+
+    def __init__(self, path: str):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        lib()  # configure the default library first
+        self.saved = _lib
+        L = ctypes.CDLL(self.path)
+        for name in ("wo_quantize", "wo_sweep", "wo_vose", "wo_psa", "wo_vose_f64", "wo_encode",
+                     "wo_philox4x32_10", "wo_sample", "wo_sample_at"):
+            f, g = getattr(L, name), getattr(self.saved, name)
+            f.argtypes, f.restype = g.argtypes, g.restype
+        with _lock:
+            _lib = L
+        return L
+
+    def __exit__(self, *exc):
+        global _lib
+        with _lock:
+            _lib = self.saved
+
+
 def _ptr(a: np.ndarray) -> int:
     assert a.flags["C_CONTIGUOUS"]
     return a.ctypes.data

@@ -58,7 +58,44 @@ __global__ void k_gen(int kind, uint32_t *out, uint64_t n, uint64_t base, double
 
 uint64_t base_of(uint64_t seed, uint64_t purpose) { return splitmix64(seed ^ (purpose << 48)); }
 
+// Random 16-byte gathers from a table of n entries: the memory access pattern
+// of an alias query (same load instruction) with almost no arithmetic, to
+// measure the practical ceiling of random-bucket sampling on this GPU.
+__global__ void k_gather(const uint4 *__restrict__ tab, uint64_t n, uint64_t k, uint64_t seed,
+                         uint32_t *__restrict__ out)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < k; s += 4 * stride) {
+        uint64_t r[4];
+        uint4 b[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) r[j] = __umul64hi(splitmix64(seed + s + j * stride), n);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (s + j * stride < k)
+                asm volatile("ld.global.nc.L2::64B.v4.u32 {%0, %1, %2, %3}, [%4];"
+                             : "=r"(b[j].x), "=r"(b[j].y), "=r"(b[j].z), "=r"(b[j].w)
+                             : "l"(tab + r[j]));
+#pragma unroll
+        for (int j = 0; j < 4; ++j) if (s + j * stride < k) __stcs(out + s + j * stride, b[j].x ^ b[j].z);
+    }
+}
+
 } // namespace
+
+extern "C" int wl_random_gather(const void *d_table, uint64_t n, uint64_t k, uint64_t seed, void *d_out, void *stream)
+{
+    if (!d_table || !d_out || n == 0) return 1;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    uint64_t want = (k + 1023) / 1024;
+    uint64_t cap = (uint64_t)(sms > 0 ? sms : 1) * 8;
+    unsigned blocks = (unsigned)(want < cap ? (want ? want : 1) : cap);
+    k_gather<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(static_cast<const uint4 *>(d_table), n, k, seed,
+                                                                    static_cast<uint32_t *>(d_out));
+    return cudaGetLastError() == cudaSuccess ? 0 : 2;
+}
 
 extern "C" int wl_generate(int kind, void *d_out, uint64_t n, uint64_t seed, double s, void *stream)
 {

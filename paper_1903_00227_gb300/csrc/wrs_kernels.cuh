@@ -911,10 +911,13 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep(const uint32_t *__restric
 }
 
 // ----------------------------------------------------------- k_sample
+// A query reads one random 16-B bucket.  The .L2::64B size hint makes the L2
+// fetch 64 B per miss instead of 128 B: half the DRAM bytes per sample, a few
+// percent faster (random sampling is bound by DRAM accesses, not bytes).
 __device__ __forceinline__ uint4 ld_bucket(const uint4 *p)
 {
     uint4 v;
-    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+    asm volatile("ld.global.nc.L2::64B.v4.u32 {%0, %1, %2, %3}, [%4];"
                  : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
                  : "l"(p));
     return v;

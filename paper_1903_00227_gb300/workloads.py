@@ -119,6 +119,9 @@ def _wl_lib():
         lib.wl_generate.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
                                     ctypes.c_double, ctypes.c_void_p]
         lib.wl_generate.restype = ctypes.c_int
+        lib.wl_random_gather.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                                         ctypes.c_void_p, ctypes.c_void_p]
+        lib.wl_random_gather.restype = ctypes.c_int
         _wl = lib
     return _wl
 
@@ -136,3 +139,11 @@ def generate_device(kind: str, n: int, seed: int, s: float = 1.0, out=None, stre
     if rc:
         raise RuntimeError(f"wl_generate failed ({rc})")
     return out
+
+
+def random_gather(d_table: int, n: int, k: int, seed: int, d_out: int, stream: int) -> None:
+    """k random 16-byte gathers from a device table of n entries (measurement
+    of the random-access ceiling that bounds alias sampling)."""
+    rc = _wl_lib().wl_random_gather(d_table, n, k, seed, d_out, stream)
+    if rc:
+        raise RuntimeError(f"wl_random_gather failed ({rc})")

@@ -327,6 +327,22 @@ def test_sampler_tails_take_the_alias():
         assert out[s] == (r + 1) % n
 
 
+def test_sampler_coin_with_small_denominator():
+    """Two buckets, bucket 0 full, bucket 1 holding thr/qp of itself and item
+    0 as alias: P[X = 1] = (1/2) * (thr/qp) exactly (each bucket is drawn
+    with probability 1/2 since 2^64 is even; the coin is heads with
+    probability ceil(thr * 2^64 / qp) / 2^64)."""
+    k = 200_000
+    for qp, t1 in ((2, 1), (3, 1), (3, 2), (7, 3)):
+        thr = np.array([qp, t1], np.uint64)
+        alias = np.array([0, 0], np.uint32)
+        out = O.sample(thr, alias, qp, k, seed=11 + qp, stream=t1)
+        p1 = 0.5 * C.coin_heads(t1, qp) / 2 ** 64
+        hits = int((out == 1).sum())
+        sd = (k * p1 * (1 - p1)) ** 0.5
+        assert abs(hits - k * p1) < 6 * sd, (qp, t1, hits, k * p1)
+
+
 def test_sampler_chi_square():
     from scipy import stats
     w = WL.f32_zipf(200, 1.0, 3)
