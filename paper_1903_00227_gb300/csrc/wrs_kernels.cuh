@@ -668,22 +668,27 @@ struct SweepSmem {
     uint32_t rng[4];      // light and heavy index ranges of the current round
 };
 
-__device__ __forceinline__ uint32_t ub_keys(const u128 *key, uint32_t lo, uint32_t hi, u128 v)
-{ // first index in [lo, hi) with key > v
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (key[swz(mid)] <= v) lo = mid + 1; else hi = mid;
+// First index in [lo, hi) of the sorted keys whose key is > v (upper) or
+// >= v (!upper), found by a whole warp: each round probes 32 evenly spaced
+// keys and keeps the gap between the last probe before the answer and the
+// first one after it, so a range of 2048 takes two rounds and a final probe
+// of at most 32 keys.  Every lane returns the answer.
+__device__ __forceinline__ uint32_t warp_search(const u128 *key, uint32_t lo, uint32_t hi, u128 v, bool upper)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    while (hi - lo > 32) {
+        const uint32_t step = (hi - lo + 31) / 32;
+        const uint32_t p = lo + step * lane;
+        const bool before = p < hi && (upper ? key[swz(p)] <= v : key[swz(p)] < v);
+        const uint32_t cnt = (uint32_t)__popc(__ballot_sync(0xFFFFFFFFu, before)); // probes before the answer
+        if (cnt == 0) return lo;
+        const uint32_t nhi = lo + step * cnt; // first probe not before the answer (or past hi)
+        lo += step * (cnt - 1) + 1;
+        hi = nhi < hi ? nhi : hi;
     }
-    return lo;
-}
-
-__device__ __forceinline__ uint32_t lb_keys(const u128 *key, uint32_t lo, uint32_t hi, u128 v)
-{ // first index in [lo, hi) with key >= v
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (key[swz(mid)] < v) lo = mid + 1; else hi = mid;
-    }
-    return lo;
+    const uint32_t p = lo + lane;
+    const bool before = p < hi && (upper ? key[swz(p)] <= v : key[swz(p)] < v);
+    return lo + (uint32_t)__popc(__ballot_sync(0xFFFFFFFFu, before));
 }
 
 // Keys of stream tile t's heavies into S.hkey/S.hoff (all threads call).
@@ -852,12 +857,13 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep(const uint32_t *__restric
             }
             const uint32_t hc = S.hcount;
             __syncthreads(); // own keys and window complete
-            if (threadIdx.x < 3) {
+            if (threadIdx.x < 3 * 32) { // one warp per search
+                const int q = threadIdx.x >> 5;
                 uint32_t r;
-                if (threadIdx.x == 0) r = lb_keys(S.okey, al, nl, S.hkey[swz(hc - 1)]); // lights answered here
-                else if (threadIdx.x == 1) r = ub_keys(S.hkey, 0, hc, D_start);         // heavies packed here:
-                else r = ub_keys(S.hkey, 0, hc, D_end);                                // E in (D_start, D_end]
-                S.rng[1 + threadIdx.x] = r;
+                if (q == 0) r = warp_search(S.okey, al, nl, S.hkey[swz(hc - 1)], false); // lights answered here
+                else if (q == 1) r = warp_search(S.hkey, 0, hc, D_start, true);          // heavies packed here:
+                else r = warp_search(S.hkey, 0, hc, D_end, true);                        // E in (D_start, D_end]
+                if ((threadIdx.x & 31) == 0) S.rng[1 + q] = r;
             }
             __syncthreads();
             const uint32_t a0 = al, a1 = S.rng[1], b0 = S.rng[2], b1 = S.rng[3];
