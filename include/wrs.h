@@ -179,6 +179,93 @@ uint32_t wrs_set_wait_limit(uint32_t polls);
 void wrs_debug_skip_publish(int64_t tile);
 
 /*
+ * Batched build and sampling of many independent tables.
+ *
+ * The paper treats one distribution; systems that draw from thousands of
+ * small and mid-sized distributions at once (Sec. 4.2 notes that PSA's
+ * subproblems are independent; Sec. 6 gives every PE its own table) pay a
+ * launch sequence per table.  A batch instead runs each stage of the build
+ * as ONE launch over all its tables, and all their samples as one more.
+ * Table t of a batch gets exactly the buckets wrs_table_build gives its
+ * weights, and exactly the samples of wrs_sample(table_t, k_t, seed,
+ * stream_id + t): batching changes no result.  A failed table (bad weight,
+ * total out of range) reports its own status and leaves the others intact.
+ *
+ * Layout: the weights of all tables sit in ONE device buffer of dtype words,
+ * table t starting at word offset[t] (each table 16-byte aligned: offsets
+ * are multiples of 4 words; the gaps are never read).  The buckets follow
+ * the same offsets in the batch's own bucket array.  Sample outputs of table
+ * t start at k_offset[t] of the caller's output buffer.
+ *
+ * Nothing passed to a launch changes between builds of the same batch
+ * (the look-back generation is kept in device memory), so the caller may
+ * capture wrs_batch_build + wrs_batch_sample in a CUDA graph and replay it
+ * after rewriting the weights in place.
+ */
+typedef struct wrs_batch wrs_batch; /* opaque; device memory owned by the library */
+
+/* Word offsets of ntables tables of h_n[t] weights (1 <= h_n[t] < 2^32) in a
+ * batch's weight buffer: h_offsets[0..ntables], the last entry the total
+ * length in words.  Host only (no device call). */
+wrs_status wrs_batch_offsets(uint32_t ntables, const uint64_t *h_n, uint64_t *h_offsets);
+
+/* Allocate a batch (buckets and workspace) for ntables tables of h_n[t]
+ * weights, 1 <= ntables < 2^31.  Synchronous.  Errors: WRS_EINVAL, WRS_ENOMEM. */
+wrs_status wrs_batch_create(uint32_t ntables, const uint64_t *h_n, wrs_batch **out);
+
+/* The batch's offsets, as wrs_batch_offsets (ntables + 1 entries). */
+wrs_status wrs_batch_layout(const wrs_batch *b, uint64_t *h_offsets);
+
+/* Device pointer to the batch's buckets (table t at offset[t]). */
+const wrs_bucket *wrs_batch_buckets(const wrs_batch *b);
+
+/* Build every table from d_weights (device, 4-byte aligned, laid out by
+ * offset[]).  Asynchronous on `stream`: seven kernel launches, no host
+ * synchronisation, no allocation.  Device-detected errors land in the
+ * tables' statuses (wrs_batch_status). */
+wrs_status wrs_batch_build(wrs_batch *b, const void *d_weights, wrs_dtype dtype, void *stream);
+
+/* Sample plan: table t draws h_k[t] samples (0 allowed).  Writes the output
+ * offsets to h_k_offsets[0..ntables] when not NULL (last entry: total).
+ * Synchronous; allocates device memory when the plan grows. */
+wrs_status wrs_batch_set_samples(wrs_batch *b, const uint64_t *h_k, uint64_t *h_k_offsets);
+
+/* Draw the planned samples of every built table into d_out (device, total
+ * entries): table t's k_t samples are those of wrs_sample with stream id
+ * stream_id + t.  One launch, asynchronous; a failed table writes nothing. */
+wrs_status wrs_batch_sample(const wrs_batch *b, uint64_t seed, uint64_t stream_id, uint32_t *d_out,
+                            void *stream);
+
+/* Synchronise and write every table's status to h_status[0..ntables-1]
+ * (may be NULL).  Returns the first failing table's status, or WRS_OK. */
+wrs_status wrs_batch_status(const wrs_batch *b, int32_t *h_status);
+
+/* Synchronise and fill *info for table `table` of the last build. */
+wrs_status wrs_batch_table_info(const wrs_batch *b, uint32_t table, wrs_table_info *info);
+
+/* Synchronise and copy all buckets (offset[ntables] of them) to h_buckets
+ * (bytes >= 16 * offset[ntables]); the gaps between tables hold no bucket. */
+wrs_status wrs_batch_download(const wrs_batch *b, void *h_buckets, uint64_t bytes);
+
+/* Autotuning of the sweep.  Tables fall in WRS_BATCH_CLASSES size classes by
+ * tiles of 2048 weights (1, 2-4, 5-32, 33-256, more); within a class every
+ * sweep block takes `group` consecutive tiles of one table (the number of
+ * split subproblems of a table is its tiles / group).  wrs_batch_tune builds
+ * the batch from d_weights, then for each class present times the sweep
+ * with group 1, 2, 4 and 8 (best of three each, CUDA events) and keeps the
+ * fastest; finally it rebuilds with the chosen groups and writes the tuned
+ * sweep time to *h_sweep_ms when not NULL.  Synchronous.  The groups change
+ * speed only, never a bucket. */
+#define WRS_BATCH_CLASSES 5
+wrs_status wrs_batch_tune(wrs_batch *b, const void *d_weights, wrs_dtype dtype, void *stream,
+                          float *h_sweep_ms);
+wrs_status wrs_batch_groups(const wrs_batch *b, uint32_t *h_groups);             /* WRS_BATCH_CLASSES entries */
+wrs_status wrs_batch_set_groups(wrs_batch *b, const uint32_t *h_groups);         /* each 1..64; synchronous */
+
+/* Free all memory of the batch (synchronises the device first).  NULL ok. */
+void wrs_batch_free(wrs_batch *b);
+
+/*
  * Build without allocating (no counterpart in the paper).
  *
  * For callers that cannot call cudaMalloc -- code running inside a CUDA graph

@@ -534,3 +534,5 @@ extern "C" wrs_status wrs_build_noalloc(const void *d_weights, uint64_t n, wrs_d
     else k_sweep<0><<<sweep_blocks, kThreads, sizeof(SweepSmem), s>>>(w, n, vec, hdr, incl, split, slist, ntiles, buckets);
     return launch_err();
 }
+
+#include "wrs_batch.cuh"

@@ -168,17 +168,19 @@ __device__ Acc acc_block_reduce(Acc a)
     return a; // valid in thread 0
 }
 
+// Block `bid` of `nblk` blocks sharing the weights of one table; thread 0
+// writes the block's partial to *out.
 template <int F32>
-__global__ void __launch_bounds__(kThreads) k_stats(const uint32_t *__restrict__ w, uint64_t n, int vec,
-                                                    Partial *__restrict__ part)
+__device__ __forceinline__ void stats_body(const uint32_t *__restrict__ w, uint64_t n, int vec, uint32_t bid,
+                                           uint32_t nblk, Partial *__restrict__ out)
 {
     Acc a;
     a.base = F32 ? INT_MAX : 0;
     a.acc = 0;
     a.flags = 0;
     uint64_t a64 = 0;
-    const uint64_t tid = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
-    const uint64_t nth = (uint64_t)gridDim.x * kThreads;
+    const uint64_t tid = (uint64_t)bid * kThreads + threadIdx.x;
+    const uint64_t nth = (uint64_t)nblk * kThreads;
     const uint64_t nv = vec ? n / 4 : 0;
     const uint4 *w4 = reinterpret_cast<const uint4 *>(w);
     uint64_t i = tid;
@@ -205,8 +207,15 @@ __global__ void __launch_bounds__(kThreads) k_stats(const uint32_t *__restrict__
     if (threadIdx.x == 0) {
         Partial p;
         p.lo = lo64(a.acc); p.hi = hi64(a.acc); p.base = a.base; p.flags = a.flags; p.pad = 0;
-        part[blockIdx.x] = p;
+        *out = p;
     }
+}
+
+template <int F32>
+__global__ void __launch_bounds__(kThreads) k_stats(const uint32_t *__restrict__ w, uint64_t n, int vec,
+                                                    Partial *__restrict__ part)
+{
+    stats_body<F32>(w, n, vec, blockIdx.x, gridDim.x, part + blockIdx.x);
 }
 
 // Is n * val(v) <= Q * 2^beta for the binary32 pattern v (v >= +0, finite)?
@@ -226,8 +235,8 @@ __device__ bool f32_light(uint32_t v, uint64_t n, u128 Q, int beta)
     return nm <= (Q << dd);
 }
 
-__global__ void __launch_bounds__(kThreads) k_stats_combine(const Partial *__restrict__ part, uint32_t nparts,
-                                                            uint64_t n, uint32_t f32, DevHeader *hdr)
+__device__ __forceinline__ void stats_combine_body(const Partial *__restrict__ part, uint32_t nparts, uint64_t n,
+                                                   uint32_t f32, DevHeader *hdr)
 {
     Acc a;
     a.base = INT_MAX; a.acc = 0; a.flags = 0;
@@ -275,6 +284,12 @@ __global__ void __launch_bounds__(kThreads) k_stats_combine(const Partial *__res
     hdr->status = status;
 }
 
+__global__ void __launch_bounds__(kThreads) k_stats_combine(const Partial *__restrict__ part, uint32_t nparts,
+                                                            uint64_t n, uint32_t f32, DevHeader *hdr)
+{
+    stats_combine_body(part, nparts, n, f32, hdr);
+}
+
 // ---------------------------------------------------------- k_classify
 // q of a weight known to be below 2^61 (shift <= 37)
 __device__ __forceinline__ uint64_t q64_of(uint32_t x, uint32_t f32, int beta)
@@ -310,10 +325,12 @@ __device__ __forceinline__ TileSum tilesum_ldcg(const TileSum *p)
     return r;
 }
 
+// Tiles t_first, t_first + t_stride, ... of one table.
 template <int F32>
-__global__ void __launch_bounds__(kThreads) k_classify(const uint32_t *__restrict__ w, uint64_t n, int vec,
-                                                       const DevHeader *__restrict__ hdr, TileSum *__restrict__ agg,
-                                                       uint16_t *__restrict__ slist, uint32_t ntiles)
+__device__ __forceinline__ void classify_body(const uint32_t *__restrict__ w, uint64_t n, int vec,
+                                              const DevHeader *__restrict__ hdr, TileSum *__restrict__ agg,
+                                              uint16_t *__restrict__ slist, uint32_t ntiles, uint32_t t_first,
+                                              uint32_t t_stride)
 {
     __shared__ u128 s_l[kWarps], s_h[kWarps];
     __shared__ uint32_t s_c[kWarps], s_first[kWarps];
@@ -322,10 +339,10 @@ __global__ void __launch_bounds__(kThreads) k_classify(const uint32_t *__restric
     const uint32_t light_max = hdr->light_max;
     const int beta = hdr->beta;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    uint32_t t = blockIdx.x;
+    uint32_t t = t_first;
     uint32_t x[kItems];
     if (t < ntiles) load_items(w, n, vec, (uint64_t)t * kTile + (uint64_t)threadIdx.x * kItems, x);
-    for (; t < ntiles; t += gridDim.x) {
+    for (; t < ntiles; t += t_stride) {
         const uint64_t first = (uint64_t)t * kTile + (uint64_t)threadIdx.x * kItems;
         uint32_t cl = 0, nh = 0, fh = kNone, lm = 0;
         // exact sums: 64-bit when every addend is below 2^61, else 128-bit
@@ -364,7 +381,7 @@ __global__ void __launch_bounds__(kThreads) k_classify(const uint32_t *__restric
         const uint32_t lm_keep = lm;
         const uint32_t cl_keep = cl, nh_keep = nh;
         // prefetch the next tile of this block
-        const uint32_t tn = t + gridDim.x;
+        const uint32_t tn = t + t_stride;
         if (tn < ntiles) load_items(w, n, vec, (uint64_t)tn * kTile + (uint64_t)threadIdx.x * kItems, x);
         // block reduction of (L, H, counts, first heavy)
         uint32_t cc = cl | (nh << 16), f = fh;
@@ -409,6 +426,14 @@ __global__ void __launch_bounds__(kThreads) k_classify(const uint32_t *__restric
     }
 }
 
+template <int F32>
+__global__ void __launch_bounds__(kThreads) k_classify(const uint32_t *__restrict__ w, uint64_t n, int vec,
+                                                       const DevHeader *__restrict__ hdr, TileSum *__restrict__ agg,
+                                                       uint16_t *__restrict__ slist, uint32_t ntiles)
+{
+    classify_body<F32>(w, n, vec, hdr, agg, slist, ntiles, blockIdx.x, gridDim.x);
+}
+
 // ---------------------------------------------------------- k_tilescan
 // Inclusive prefix of the tile aggregates.  Each block takes 256 consecutive
 // tiles (block ids in launch order from an atomic counter, so every block it
@@ -435,11 +460,10 @@ __device__ __forceinline__ TileSum tilesum_shfl_xor(const TileSum &a, int m)
     return b;
 }
 
-__global__ void __launch_bounds__(kThreads) k_tilescan(DevHeader *hdr, const TileSum *__restrict__ agg,
-                                                       TileSum *chunk_agg, TileSum *chunk_incl,
-                                                       TileSum *__restrict__ incl, uint32_t *flags,
-                                                       uint32_t ntiles, uint32_t epoch, uint32_t wait_limit,
-                                                       uint32_t skip_chunk)
+__device__ __forceinline__ void tilescan_body(DevHeader *hdr, const TileSum *__restrict__ agg, TileSum *chunk_agg,
+                                              TileSum *chunk_incl, TileSum *__restrict__ incl, uint32_t *flags,
+                                              uint32_t ntiles, uint32_t epoch, uint32_t wait_limit,
+                                              uint32_t skip_chunk)
 {
     __shared__ uint32_t s_chunk, s_status;
     __shared__ U2 s_scan[kWarps];
@@ -528,6 +552,15 @@ __global__ void __launch_bounds__(kThreads) k_tilescan(DevHeader *hdr, const Til
     }
 }
 
+__global__ void __launch_bounds__(kThreads) k_tilescan(DevHeader *hdr, const TileSum *__restrict__ agg,
+                                                       TileSum *chunk_agg, TileSum *chunk_incl,
+                                                       TileSum *__restrict__ incl, uint32_t *flags,
+                                                       uint32_t ntiles, uint32_t epoch, uint32_t wait_limit,
+                                                       uint32_t skip_chunk)
+{
+    tilescan_body(hdr, agg, chunk_agg, chunk_incl, incl, flags, ntiles, epoch, wait_limit, skip_chunk);
+}
+
 // ------------------------------------------------------------ k_split
 // For every tile c, from the tile prefix sums: with D_c = D at the first
 // light of tile c and E_c = E after the heavies before tile c,
@@ -559,11 +592,11 @@ __device__ __forceinline__ Prefix prefix_at(const TileSum *incl, uint32_t b, uin
 __device__ __forceinline__ u128 key_E(const Prefix &p, uint64_t n, u128 Q) { return times_n(p.H, n) - (u128)p.ch * Q; }
 __device__ __forceinline__ u128 key_D(const Prefix &p, uint64_t n, u128 Q) { return (u128)p.cl * Q - times_n(p.L, n); }
 
-__global__ void __launch_bounds__(kThreads) k_split(const TileSum *__restrict__ incl, uint32_t ntiles, uint64_t n,
-                                                    DevHeader *hdr, Split *__restrict__ split)
+// Tile c of one table (one thread per tile).
+__device__ __forceinline__ void split_body(const TileSum *__restrict__ incl, uint32_t ntiles, uint64_t n,
+                                           DevHeader *hdr, Split *__restrict__ split, uint32_t c)
 {
     if (*(volatile uint32_t *)&hdr->status) return;
-    const uint32_t c = blockIdx.x * kThreads + threadIdx.x;
     const u128 Q = mk128(hdr->q_lo, hdr->q_hi);
     const uint64_t n_light = load_prefix(incl, ntiles).cl;
     if (c == 0) hdr->n_light = n_light;
@@ -597,6 +630,12 @@ __global__ void __launch_bounds__(kThreads) k_split(const TileSum *__restrict__ 
     Split s;
     s.hb = hb; s.lb = lb; s.next_heavy = nxt; s.pad = 0;
     split[c] = s;
+}
+
+__global__ void __launch_bounds__(kThreads) k_split(const TileSum *__restrict__ incl, uint32_t ntiles, uint64_t n,
+                                                    DevHeader *hdr, Split *__restrict__ split)
+{
+    split_body(incl, ntiles, n, hdr, split, blockIdx.x * kThreads + threadIdx.x);
 }
 
 
@@ -759,12 +798,12 @@ __device__ __forceinline__ void load_heavies(SweepSmem &S, uint32_t t, const uin
 
 constexpr int kSweepTiles = 4; // own tiles per block of k_sweep (they share stream tiles)
 
+// Own tiles [c_first, c_last) of one table.
 template <int F32>
-__global__ void __launch_bounds__(kThreads, 3) k_sweep(const uint32_t *__restrict__ w, uint64_t n, int vec,
-                                                       DevHeader *hdr, const TileSum *__restrict__ incl,
-                                                       const Split *__restrict__ split,
-                                                       const uint16_t *__restrict__ slist, uint32_t ntiles,
-                                                       uint4 *__restrict__ table)
+__device__ __forceinline__ void sweep_body(const uint32_t *__restrict__ w, uint64_t n, int vec, DevHeader *hdr,
+                                           const TileSum *__restrict__ incl, const Split *__restrict__ split,
+                                           const uint16_t *__restrict__ slist, uint32_t ntiles,
+                                           uint4 *__restrict__ table, uint32_t c_first, uint32_t c_last)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SweepSmem &S = *reinterpret_cast<SweepSmem *>(smem_raw);
@@ -774,8 +813,6 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep(const uint32_t *__restric
     const uint32_t light_max = hdr->light_max;
     const int beta = hdr->beta;
     const uint32_t shift = hdr->shift;
-    const uint32_t c_first = blockIdx.x * kSweepTiles;
-    const uint32_t c_last = min(c_first + kSweepTiles, ntiles);
     bool bad = false;
 
     uint32_t x[kItems], y[kItems];
@@ -916,6 +953,17 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep(const uint32_t *__restric
     if (bad) set_status(hdr, kEInternal);
 }
 
+template <int F32>
+__global__ void __launch_bounds__(kThreads, 3) k_sweep(const uint32_t *__restrict__ w, uint64_t n, int vec,
+                                                       DevHeader *hdr, const TileSum *__restrict__ incl,
+                                                       const Split *__restrict__ split,
+                                                       const uint16_t *__restrict__ slist, uint32_t ntiles,
+                                                       uint4 *__restrict__ table)
+{
+    const uint32_t c_first = blockIdx.x * kSweepTiles;
+    sweep_body<F32>(w, n, vec, hdr, incl, split, slist, ntiles, table, c_first, min(c_first + kSweepTiles, ntiles));
+}
+
 // ----------------------------------------------------------- k_sample
 // A query reads one random 16-B bucket.  The .L2::64B size hint makes the L2
 // fetch 64 B per miss instead of 128 B: half the DRAM bytes per sample, a few
@@ -931,15 +979,12 @@ __device__ __forceinline__ uint4 ld_bucket(const uint4 *p)
 
 constexpr int kSampleUnroll = 4;
 
-__global__ void __launch_bounds__(256) k_sample(const uint4 *__restrict__ tab, uint64_t n,
-                                                const DevHeader *__restrict__ hdr, uint64_t k, uint32_t key0,
-                                                uint32_t key1, uint32_t sid0, uint32_t sid1,
-                                                uint32_t *__restrict__ out)
+// Samples first, first + stride, ... (below k) of one table.
+__device__ __forceinline__ void sample_body(const uint4 *__restrict__ tab, uint64_t n, uint64_t qp, uint64_t k,
+                                            uint32_t key0, uint32_t key1, uint32_t sid0, uint32_t sid1,
+                                            uint32_t *__restrict__ out, uint64_t first, uint64_t stride)
 {
-    if (hdr->status) return;
-    const uint64_t qp = hdr->qp;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < k; s += kSampleUnroll * stride) {
+    for (uint64_t s = first; s < k; s += kSampleUnroll * stride) {
         uint64_t r[kSampleUnroll], v[kSampleUnroll];
         uint4 b[kSampleUnroll];
 #pragma unroll
@@ -965,6 +1010,16 @@ __global__ void __launch_bounds__(256) k_sample(const uint4 *__restrict__ tab, u
             }
         }
     }
+}
+
+__global__ void __launch_bounds__(256) k_sample(const uint4 *__restrict__ tab, uint64_t n,
+                                                const DevHeader *__restrict__ hdr, uint64_t k, uint32_t key0,
+                                                uint32_t key1, uint32_t sid0, uint32_t sid1,
+                                                uint32_t *__restrict__ out)
+{
+    if (hdr->status) return;
+    sample_body(tab, n, hdr->qp, k, key0, key1, sid0, sid1, out, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                (uint64_t)gridDim.x * blockDim.x);
 }
 
 } // namespace wrs

@@ -101,6 +101,30 @@ def generate(kind: str, n: int, seed: int, s: float = 1.0) -> np.ndarray:
     raise ValueError(kind)
 
 
+# ------------------------------------------------------- many distributions
+PURPOSE_BATCH = 3
+
+
+def log_uniform_ints(count: int, lo: int, hi: int, seed: int, purpose: int) -> np.ndarray:
+    """count integers log-uniform on [lo, hi]: floor(lo * (hi + 1 / lo)^u), u
+    the top 53 bits of a SplitMix64 word, clipped to [lo, hi]."""
+    u = (words(count, seed, purpose) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    v = np.floor(np.exp(np.log(lo) + u * (np.log(hi + 1) - np.log(lo))))
+    return np.clip(v, lo, hi).astype(np.int64)
+
+
+def batch_plan(ntables: int, seed: int, n_lo: int = 32, n_hi: int = 1 << 20, k_lo: int = 1, k_hi: int = 4096):
+    """Many independent distributions: per table its size n (log-uniform in
+    [n_lo, n_hi]), its sample count k (log-uniform in [k_lo, k_hi]), its kind
+    (binary32 uniform or Zipf s = 1.0, one random bit) and its weight seed."""
+    n = log_uniform_ints(ntables, n_lo, n_hi, seed, PURPOSE_BATCH)
+    k = log_uniform_ints(ntables, k_lo, k_hi, seed ^ 0x5A5A5A5A, PURPOSE_BATCH)
+    bit = words(ntables, seed ^ 0xA5A5A5A5, PURPOSE_BATCH) & np.uint64(1)
+    kinds = ["f32_zipf" if b else "f32_uniform" for b in bit]
+    seeds = [int(seed) * 1_000_003 + t for t in range(ntables)]
+    return [int(x) for x in n], [int(x) for x in k], kinds, seeds
+
+
 # --------------------------------------------------------------- device side
 KINDS = {"u32_uniform": 0, "f32_uniform": 1, "f32_zipf": 2}
 _wl = None

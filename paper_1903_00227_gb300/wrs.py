@@ -73,6 +73,20 @@ _sig = {
     "wrs_set_wait_limit": ([ctypes.c_uint32], ctypes.c_uint32),
     "wrs_debug_skip_publish": ([ctypes.c_int64], None),
     "wrs_build_noalloc": ([_P, _U64, _I, _P, _P, _P], _I),
+    "wrs_batch_offsets": ([ctypes.c_uint32, _P, _P], _I),
+    "wrs_batch_create": ([ctypes.c_uint32, _P, _PTBL], _I),
+    "wrs_batch_layout": ([_TBL, _P], _I),
+    "wrs_batch_buckets": ([_TBL], _P),
+    "wrs_batch_build": ([_TBL, _P, _I, _P], _I),
+    "wrs_batch_set_samples": ([_TBL, _P, _P], _I),
+    "wrs_batch_sample": ([_TBL, _U64, _U64, _P, _P], _I),
+    "wrs_batch_status": ([_TBL, _P], _I),
+    "wrs_batch_table_info": ([_TBL, ctypes.c_uint32, ctypes.POINTER(TableInfo)], _I),
+    "wrs_batch_tune": ([_TBL, _P, _I, _P, ctypes.POINTER(ctypes.c_float)], _I),
+    "wrs_batch_groups": ([_TBL, _P], _I),
+    "wrs_batch_set_groups": ([_TBL, _P], _I),
+    "wrs_batch_download": ([_TBL, _P, _U64], _I),
+    "wrs_batch_free": ([_TBL], None),
 }
 for _name, (_args, _res) in _sig.items():
     _f = getattr(_lib, _name)
@@ -183,6 +197,83 @@ def build_noalloc(d_weights: int, n: int, dtype: int, d_buckets: int, d_header: 
     return _lib.wrs_build_noalloc(d_weights, n, dtype, d_buckets, d_header, stream)
 
 
+BATCH_CLASSES = 5
+
+
+def _u64_array(values):
+    vals = [int(v) for v in values]
+    return (ctypes.c_uint64 * max(1, len(vals)))(*vals)
+
+
+def batch_offsets(sizes):
+    """wrs_batch_offsets: (rc, word offsets of the tables, total words last)."""
+    arr = _u64_array(sizes)
+    out = (ctypes.c_uint64 * (len(sizes) + 1))()
+    rc = _lib.wrs_batch_offsets(len(sizes), arr, out)
+    return rc, [int(x) for x in out]
+
+
+def batch_create(sizes):
+    h = ctypes.c_void_p()
+    rc = _lib.wrs_batch_create(len(sizes), _u64_array(sizes), ctypes.byref(h))
+    return rc, h.value
+
+
+def batch_build(b, d_weights: int, dtype: int, stream: int = 0) -> int:
+    return _lib.wrs_batch_build(b, d_weights, dtype, stream)
+
+
+def batch_set_samples(b, ks):
+    out = (ctypes.c_uint64 * (len(ks) + 1))()
+    rc = _lib.wrs_batch_set_samples(b, _u64_array(ks), out)
+    return rc, [int(x) for x in out]
+
+
+def batch_sample(b, seed: int, stream_id: int, d_out: int, stream: int = 0) -> int:
+    return _lib.wrs_batch_sample(b, seed, stream_id, d_out, stream)
+
+
+def batch_status(b, ntables: int):
+    st = (ctypes.c_int32 * ntables)()
+    rc = _lib.wrs_batch_status(b, st)
+    return rc, [int(x) for x in st]
+
+
+def batch_table_info(b, table: int):
+    info = TableInfo()
+    rc = _lib.wrs_batch_table_info(b, table, ctypes.byref(info))
+    return rc, info
+
+
+def batch_tune(b, d_weights: int, dtype: int, stream: int = 0):
+    ms = ctypes.c_float()
+    rc = _lib.wrs_batch_tune(b, d_weights, dtype, stream, ctypes.byref(ms))
+    return rc, float(ms.value)
+
+
+def batch_groups(b):
+    g = (ctypes.c_uint32 * BATCH_CLASSES)()
+    rc = _lib.wrs_batch_groups(b, g)
+    return rc, [int(x) for x in g]
+
+
+def batch_set_groups(b, groups) -> int:
+    g = (ctypes.c_uint32 * BATCH_CLASSES)(*[int(x) for x in groups])
+    return _lib.wrs_batch_set_groups(b, g)
+
+
+def batch_buckets(b) -> int:
+    return _lib.wrs_batch_buckets(b) or 0
+
+
+def batch_download(b, h_buckets: int, nbytes: int) -> int:
+    return _lib.wrs_batch_download(b, h_buckets, nbytes)
+
+
+def batch_free(b) -> None:
+    _lib.wrs_batch_free(b)
+
+
 # --- convenience wrapper over torch tensors --------------------------------
 def _dtype_code(t) -> int:
     import torch
@@ -272,3 +363,106 @@ class AliasTable:
             self.free()
         except Exception:
             pass
+
+
+class AliasBatch:
+    """Owns a batch of independent device-resident alias tables (``wrs_batch``).
+
+    ``weights`` buffers are laid out by ``offsets`` (table t at word
+    ``offsets[t]``); ``pack`` builds such a buffer from a list of tensors."""
+
+    def __init__(self, sizes):
+        self.sizes = [int(x) for x in sizes]
+        rc, h = batch_create(self.sizes)
+        _check(rc, "wrs_batch_create")
+        self.handle = h
+        rc, self.offsets = batch_offsets(self.sizes)
+        _check(rc, "wrs_batch_offsets")
+        self.k_offsets = None
+
+    @property
+    def ntables(self) -> int:
+        return len(self.sizes)
+
+    def pack(self, tensors, dtype=None):
+        """One CUDA weight buffer holding the given per-table tensors at their offsets."""
+        import torch
+
+        dtype = dtype or tensors[0].dtype
+        buf = torch.zeros(self.offsets[-1], dtype=dtype, device="cuda")
+        for t, x in enumerate(tensors):
+            assert x.numel() == self.sizes[t]
+            buf[self.offsets[t]:self.offsets[t] + self.sizes[t]].copy_(x.reshape(-1))
+        return buf
+
+    def build(self, weights, stream=None) -> "AliasBatch":
+        assert weights.is_cuda and weights.is_contiguous() and weights.numel() >= self.offsets[-1]
+        _check(batch_build(self.handle, weights.data_ptr(), _dtype_code(weights), _stream_handle(stream)),
+               "wrs_batch_build")
+        return self
+
+    def set_samples(self, ks) -> list:
+        assert len(ks) == self.ntables
+        rc, self.k_offsets = batch_set_samples(self.handle, ks)
+        _check(rc, "wrs_batch_set_samples")
+        return self.k_offsets
+
+    def sample(self, seed: int, stream_id: int = 0, out=None, stream=None):
+        import torch
+
+        total = self.k_offsets[-1] if self.k_offsets else 0
+        if out is None:
+            out = torch.empty(max(total, 1), dtype=torch.int32, device="cuda")
+        assert out.is_cuda and out.is_contiguous() and out.numel() >= total and out.element_size() == 4
+        _check(batch_sample(self.handle, seed, stream_id, out.data_ptr(), _stream_handle(stream)),
+               "wrs_batch_sample")
+        return out
+
+    def status(self):
+        return batch_status(self.handle, self.ntables)
+
+    def info(self, table: int) -> TableInfo:
+        rc, info = batch_table_info(self.handle, table)
+        _check(rc, "wrs_batch_table_info")
+        return info
+
+    def tune(self, weights, stream=None) -> float:
+        rc, ms = batch_tune(self.handle, weights.data_ptr(), _dtype_code(weights), _stream_handle(stream))
+        _check(rc, "wrs_batch_tune")
+        return ms
+
+    def groups(self):
+        rc, g = batch_groups(self.handle)
+        _check(rc, "wrs_batch_groups")
+        return g
+
+    def set_groups(self, groups) -> None:
+        _check(batch_set_groups(self.handle, groups), "wrs_batch_set_groups")
+
+    def download(self):
+        """(thr, alias, reserved) numpy arrays over all buckets (table t at offsets[t])."""
+        import numpy as np
+
+        total = self.offsets[-1]
+        buf = np.empty(total * 2, dtype=np.uint64)
+        _check(batch_download(self.handle, buf.ctypes.data, buf.nbytes), "wrs_batch_download")
+        words = buf.view(np.uint32).reshape(total, 4)
+        return buf.reshape(total, 2)[:, 0].copy(), words[:, 2].copy(), words[:, 3].copy()
+
+    def free(self) -> None:
+        if self.handle:
+            batch_free(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.free()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+

@@ -56,3 +56,19 @@ def test_status_strings(wrs):
 def test_bucket_layout_matches_header():
     text = open(os.path.join(ROOT, "include", "wrs.h")).read()
     assert re.search(r"uint64_t thr;\s*uint32_t alias;\s*uint32_t reserved;", text)
+
+
+def test_batch_offsets_host_only(wrs):
+    sizes = [1, 2, 3, 4, 5, 2048, 2049, 7]
+    rc, off = wrs.batch_offsets(sizes)
+    assert rc == wrs.OK and len(off) == len(sizes) + 1 and off[0] == 0
+    for t, n in enumerate(sizes):
+        assert off[t] % 4 == 0, "each table starts 16-byte aligned"
+        assert off[t] + n <= off[t + 1] < off[t] + n + 4, "tables are packed in order"
+    assert wrs.batch_offsets([3, 0])[0] == wrs.EINVAL
+    assert wrs.batch_offsets([1 << 32])[0] == wrs.EINVAL
+    assert wrs.batch_create([])[0] == wrs.EINVAL
+    assert wrs.batch_build(None, 0, wrs.F32, 0) == wrs.EINVAL
+    assert wrs.batch_sample(None, 1, 0, 0, 0) == wrs.EINVAL
+    assert wrs.batch_buckets(None) == 0
+    wrs.batch_free(None)
