@@ -65,6 +65,9 @@ def parse():
                     help="weights (and samples) per distribution for the CPU-oracle baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--batch-tables", type=int, default=4096,
+                    help="tables of the many-distribution workload (0: skip it)")
+    ap.add_argument("--batch-steps", type=int, default=10)
     return ap.parse_args()
 
 
@@ -250,6 +253,97 @@ def run_reference(args, names):
     return 0
 
 
+def run_batched(args, torch, WL, wrs, stream):
+    """Many-distribution workload: 4096 tables, sizes log-uniform in [32, 2^20],
+    binary32 uniform or Zipf(1.0) by seed, k log-uniform in [1, 4096].  One
+    step builds and samples every table.  The batched path (seven build
+    launches + one sample launch over all tables, captured once in a CUDA
+    graph, sweep grouping from the autotuner) against the plain path (one
+    wrs_table per distribution: its build and sample calls, table after
+    table, on one stream).  Both must give the same samples."""
+    sh = stream.cuda_stream
+    n, k, kinds, seeds = WL.batch_plan(args.batch_tables, 4)
+    batch = wrs.AliasBatch(n)
+    off = batch.offsets
+    buf = torch.empty(off[-1], dtype=torch.float32, device="cuda")
+    for t in range(len(n)):
+        WL.generate_device(kinds[t], n[t], seeds[t], 1.0, out=buf[off[t]:off[t] + n[t]])
+    koff = batch.set_samples(k)
+    out_b = torch.empty(max(koff[-1], 1), dtype=torch.int32, device="cuda")
+    out_p = torch.empty_like(out_b)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tuned_ms = batch.tune(buf, stream=sh)
+    tune_s = time.perf_counter() - t0
+    for _ in range(3):
+        batch.build(buf, stream=sh)
+        batch.sample(11, 0, out=out_b, stream=sh)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):  # captured on torch's side stream, replayed on `stream`
+        batch.build(buf)
+        batch.sample(11, 0, out=out_b)
+    for _ in range(3):
+        graph.replay()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.batch_steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        graph.replay()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    rc, st = batch.status()
+    if rc != wrs.OK:
+        raise RuntimeError(f"batched build failed: {wrs.status_str(rc)}")
+
+    tables = [wrs.AliasTable(nt) for nt in n]
+    views = [buf[off[t]:off[t] + n[t]] for t in range(len(n))]
+    outs = [out_p[koff[t]:koff[t] + k[t]] for t in range(len(n))]
+
+    def plain_step():
+        for t, tab in enumerate(tables):
+            tab.build(views[t], stream=sh)
+            if k[t]:
+                tab.sample(k[t], 11, t, out=outs[t], stream=sh)
+
+    plain_step()
+    torch.cuda.synchronize()
+    ptimes = []
+    for _ in range(max(2, args.batch_steps // 3)):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plain_step()
+        e1.record(stream)
+        e1.synchronize()
+        ptimes.append(e0.elapsed_time(e1))
+    identical = bool(torch.equal(out_b[:koff[-1]], out_p[:koff[-1]]))
+    for tab in tables:
+        tab.free()
+    groups = batch.groups()
+    batch.free()
+    total_w, total_k = sum(n), sum(k)
+    bms, pms = statistics.mean(times), statistics.mean(ptimes)
+    srt = sorted(times)
+    return {
+        "workload": f"{len(n)} tables, sizes log-uniform in [32, 2^20] (total {total_w} binary32 weights), "
+                    f"uniform (0,1] or Zipf 1.0 by seed, k log-uniform in [1, 4096] (total {total_k})",
+        "batched": {"ms_per_step": bms, "p99_ms": srt[min(len(srt) - 1, int(round(0.99 * (len(srt) - 1))))],
+                    "gweights_s": total_w / (bms * 1e-3) / 1e9, "tables_per_s": len(n) / (bms * 1e-3),
+                    "launches_per_step": 8, "cuda_graph": True, "tuned_groups": groups,
+                    "tuned_sweep_ms": tuned_ms, "tune_seconds": tune_s},
+        "plain": {"ms_per_step": pms, "gweights_s": total_w / (pms * 1e-3) / 1e9,
+                  "tables_per_s": len(n) / (pms * 1e-3),
+                  "launches_per_step": 7 * len(n) + sum(1 for x in k if x),
+                  "note": "one wrs_table per distribution, wrs_table_build + wrs_sample per table on one stream"},
+        "speedup": pms / bms,
+        "identical_samples": identical,
+    }
+
+
 def run_ours(args, names):
     import torch
 
@@ -391,6 +485,10 @@ def run_ours(args, names):
                "d2h_bytes_per_step": 4 * k, "ms_per_step": t_e2e,
                "note": "wrs_table_build_host (H2D of the weights) + wrs_sample_host (D2H of the samples)"}
 
+    batched = None
+    if args.batch_tables > 0:
+        batched = run_batched(args, torch, WL, wrs, stream)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(names, min(args.cpu_sample, n))
@@ -410,7 +508,7 @@ def run_ours(args, names):
                                "frac": ach_build / peak, "algorithmic_bytes_per_weight": BUILD_BYTES_PER_WEIGHT,
                                "peak_source": peak_kind},
             "kernels": per_kernel, "per_dist": per_dist,
-            "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
+            "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "many_tables": batched,
             "gpu_launches": K * (len(wrs.STAGES) + 1),
             "context": {"paper_psa_build_gweights_s_n1e9": 0.99, "paper_psa_query_gsamples_s_n1e9": 1.662,
                         "paper_hardware": "4x Xeon Gold 6138, 158 threads (context only)"},
