@@ -266,6 +266,40 @@ wrs_status wrs_batch_set_groups(wrs_batch *b, const uint32_t *h_groups);        
 void wrs_batch_free(wrs_batch *b);
 
 /*
+ * Many sample requests in one launch (serving; no counterpart in the paper).
+ *
+ * A request server coalesces the sample requests that arrive while the GPU
+ * is busy into one launch over all the tables they name.  Task i draws k
+ * samples from the table (buckets, header) exactly as wrs_sample(table, k,
+ * seed, stream_id) would, into d_out[out_offset ...]: coalescing changes no
+ * result.
+ *
+ *   d_tasks   device array of ntasks tasks (16-byte aligned), ordered by
+ *             out_offset with out_offset[i+1] = out_offset[i] + k[i]
+ *             (k = 0 allowed); buckets/header point into a built table that
+ *             stays resident until the launch completes
+ *   total_k   out_offset + k of the last task; d_out holds total_k entries
+ *
+ * Asynchronous on `stream`; one launch; a task whose table failed to build
+ * writes nothing.  Errors returned at once: WRS_EINVAL. */
+typedef struct {
+    const wrs_bucket *buckets; /* device: the table's n buckets */
+    const void *header;        /* device: wrs_table_device_header / wrs_batch_device_header */
+    uint64_t n;                /* buckets of the table */
+    uint64_t k;                /* samples to draw */
+    uint64_t seed, stream_id;  /* as wrs_sample */
+    uint64_t out_offset;       /* first output entry */
+    uint64_t reserved;         /* zero */
+} wrs_sample_task;
+
+wrs_status wrs_sample_many(const wrs_sample_task *d_tasks, uint32_t ntasks, uint64_t total_k,
+                           uint32_t *d_out, void *stream);
+
+/* Device address of a table's header (for wrs_sample_task.header). */
+const void *wrs_table_device_header(const wrs_table *t);
+const void *wrs_batch_device_header(const wrs_batch *b, uint32_t table);
+
+/*
  * Build without allocating (no counterpart in the paper).
  *
  * For callers that cannot call cudaMalloc -- code running inside a CUDA graph

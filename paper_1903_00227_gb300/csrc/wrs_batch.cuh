@@ -128,6 +128,53 @@ __global__ void __launch_bounds__(256) kb_sample(const BatchTable *__restrict__ 
                 out + T.k_off, (uint64_t)m.local * 256 + threadIdx.x, (uint64_t)T.sblocks * 256);
 }
 
+// Many sample requests against many resident tables in one launch.  Task i
+// draws k_i samples into out[out_offset_i ...]; the tasks' outputs are
+// consecutive (out_offset ascending, each the previous one plus its k).
+// Block b covers outputs [b * kManyPerBlock, ...): thread 0 finds the task
+// holding the first one by binary search, then the block walks the tasks
+// that overlap its range.  Sample s of a task is sample s of wrs_sample on
+// its table with the task's seed and stream id.
+constexpr uint32_t kManyPerBlock = 256 * 16;
+
+struct SampleTask {       // mirrors wrs_sample_task
+    const uint4 *buckets;
+    const DevHeader *hdr;
+    uint64_t n, k, seed, stream_id, out_offset, reserved;
+};
+
+static_assert(sizeof(SampleTask) == sizeof(wrs_sample_task), "layout");
+static_assert(offsetof(SampleTask, hdr) == offsetof(wrs_sample_task, header), "layout");
+static_assert(offsetof(SampleTask, k) == offsetof(wrs_sample_task, k), "layout");
+static_assert(offsetof(SampleTask, out_offset) == offsetof(wrs_sample_task, out_offset), "layout");
+
+__global__ void __launch_bounds__(256) k_sample_many(const SampleTask *__restrict__ tasks, uint32_t ntasks,
+                                                     uint64_t total_k, uint32_t *__restrict__ out)
+{
+    __shared__ uint32_t s_first;
+    const uint64_t begin = (uint64_t)blockIdx.x * kManyPerBlock;
+    const uint64_t end = min(begin + kManyPerBlock, total_k);
+    if (threadIdx.x == 0) { // last task with out_offset <= begin
+        uint32_t lo = 0, hi = ntasks - 1;
+        while (lo < hi) {
+            const uint32_t mid = lo + (hi - lo + 1) / 2;
+            if (tasks[mid].out_offset <= begin) lo = mid; else hi = mid - 1;
+        }
+        s_first = lo;
+    }
+    __syncthreads();
+    for (uint32_t i = s_first; i < ntasks; ++i) {
+        const SampleTask T = tasks[i];
+        if (T.out_offset >= end) break;
+        const uint64_t lo = max(begin, T.out_offset), hi = min(end, T.out_offset + T.k);
+        if (lo >= hi || T.hdr->status) continue;
+        // local sample indices [lo - off, hi - off), written at out + off + s
+        sample_body(T.buckets, T.n, T.hdr->qp, hi - T.out_offset, (uint32_t)T.seed, (uint32_t)(T.seed >> 32),
+                    (uint32_t)T.stream_id, (uint32_t)(T.stream_id >> 32), out + T.out_offset,
+                    lo - T.out_offset + threadIdx.x, 256);
+    }
+}
+
 } // namespace wrs
 
 struct wrs_batch {
@@ -523,6 +570,29 @@ wrs_status wrs_batch_tune(wrs_batch *b, const void *d_weights, wrs_dtype dtype, 
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return st;
+}
+
+const void *wrs_batch_device_header(const wrs_batch *b, uint32_t table)
+{
+    return (b && table < b->ntables) ? static_cast<const void *>(b->hdr + table) : nullptr;
+}
+
+const void *wrs_table_device_header(const wrs_table *t)
+{
+    return t ? static_cast<const void *>(t->hdr) : nullptr;
+}
+
+wrs_status wrs_sample_many(const wrs_sample_task *d_tasks, uint32_t ntasks, uint64_t total_k, uint32_t *d_out,
+                           void *stream)
+{
+    if (total_k == 0) return WRS_OK;
+    if (!d_tasks || ntasks == 0 || !d_out) return WRS_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_tasks) % 16) != 0) return WRS_EINVAL;
+    const uint64_t blocks = (total_k + kManyPerBlock - 1) / kManyPerBlock;
+    if (blocks >= (1ull << 31)) return WRS_EINVAL;
+    k_sample_many<<<(uint32_t)blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        reinterpret_cast<const SampleTask *>(d_tasks), ntasks, total_k, d_out);
+    return launch_err();
 }
 
 void wrs_batch_free(wrs_batch *b)

@@ -87,6 +87,9 @@ _sig = {
     "wrs_batch_set_groups": ([_TBL, _P], _I),
     "wrs_batch_download": ([_TBL, _P, _U64], _I),
     "wrs_batch_free": ([_TBL], None),
+    "wrs_sample_many": ([_P, ctypes.c_uint32, _U64, _P, _P], _I),
+    "wrs_table_device_header": ([_TBL], _P),
+    "wrs_batch_device_header": ([_TBL, ctypes.c_uint32], _P),
 }
 for _name, (_args, _res) in _sig.items():
     _f = getattr(_lib, _name)
@@ -272,6 +275,21 @@ def batch_download(b, h_buckets: int, nbytes: int) -> int:
 
 def batch_free(b) -> None:
     _lib.wrs_batch_free(b)
+
+
+SAMPLE_TASK_BYTES = 64  # wrs_sample_task: 8 little-endian 64-bit words
+
+
+def sample_many(d_tasks: int, ntasks: int, total_k: int, d_out: int, stream: int = 0) -> int:
+    return _lib.wrs_sample_many(d_tasks, ntasks, total_k, d_out, stream)
+
+
+def table_device_header(t) -> int:
+    return _lib.wrs_table_device_header(t) or 0
+
+
+def batch_device_header(b, table: int) -> int:
+    return _lib.wrs_batch_device_header(b, table) or 0
 
 
 # --- convenience wrapper over torch tensors --------------------------------
