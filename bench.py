@@ -68,6 +68,9 @@ def parse():
     ap.add_argument("--batch-tables", type=int, default=4096,
                     help="tables of the many-distribution workload (0: skip it)")
     ap.add_argument("--batch-steps", type=int, default=10)
+    ap.add_argument("--serve-requests", type=int, default=100_000,
+                    help="requests of the serving workload (0: skip it)")
+    ap.add_argument("--serve-rate", type=float, default=20_000.0, help="Poisson arrival rate, requests/s")
     return ap.parse_args()
 
 
@@ -344,6 +347,34 @@ def run_batched(args, torch, WL, wrs, stream):
     }
 
 
+def run_serving(args, torch):
+    """Serving workload: a seeded Poisson stream of requests, 30% build+sample
+    (binary32 Zipf 1.0 weights uploaded from pinned host memory, sizes
+    log-uniform in [2^10, 2^24]) and 70% sample-only against resident tables,
+    k log-uniform in [1, 10^5], under a 40 GB device-memory budget with LRU
+    eviction.  The continuous-batching server against the plain path (one
+    request at a time) on the same stream; both must give the same samples."""
+    from paper_1903_00227_gb300 import serve as S
+
+    reqs = S.request_stream(args.serve_requests, rate=args.serve_rate, seed=5)
+    srv = S.Server(budget=40 << 30, max_inflight=3, tick_requests=2048, tick_samples=1 << 24)
+    t0 = time.perf_counter()
+    reserved = srv.reserve(reqs)
+    setup_s = time.perf_counter() - t0
+    served = srv.run(reqs)
+    srv.cache.clear_resident()
+    plain = srv.run_plain(reqs)
+    same = bool((served["checksum"] == plain["checksum"]).all())
+    out = {"workload": f"{len(reqs)} requests, Poisson {args.serve_rate:g}/s, 30% build+sample (Zipf 1.0, "
+                       f"n log-uniform in [2^10, 2^24]), 70% sample-only, k log-uniform in [1, 10^5], "
+                       f"40 GB budget, LRU eviction",
+           "served": S.summarize(served, reqs), "plain": S.summarize(plain, reqs),
+           "identical_samples": same, "table_objects_reserved": reserved, "reserve_seconds": setup_s,
+           "objects_created_total": srv.cache.created, "objects_freed": srv.cache.freed}
+    srv.close()
+    return out
+
+
 def run_ours(args, names):
     import torch
 
@@ -488,6 +519,9 @@ def run_ours(args, names):
     batched = None
     if args.batch_tables > 0:
         batched = run_batched(args, torch, WL, wrs, stream)
+    serving = None
+    if args.serve_requests > 0:
+        serving = run_serving(args, torch)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -508,7 +542,7 @@ def run_ours(args, names):
                                "frac": ach_build / peak, "algorithmic_bytes_per_weight": BUILD_BYTES_PER_WEIGHT,
                                "peak_source": peak_kind},
             "kernels": per_kernel, "per_dist": per_dist,
-            "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "many_tables": batched,
+            "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "many_tables": batched, "serving": serving,
             "gpu_launches": K * (len(wrs.STAGES) + 1),
             "context": {"paper_psa_build_gweights_s_n1e9": 0.99, "paper_psa_query_gsamples_s_n1e9": 1.662,
                         "paper_hardware": "4x Xeon Gold 6138, 158 threads (context only)"},

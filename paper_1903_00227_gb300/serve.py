@@ -12,8 +12,10 @@ or samples a table that is already resident.  The server runs ticks:
   ``tick_requests`` requests and ``tick_samples`` samples per tick) and the
   device-memory budget can hold the tables it needs; least-recently-used
   resident tables that no in-flight tick uses are evicted to make room;
-* device work of a tick: the builds of the tick on ``build_streams`` streams
-  (tables come from per-size-class pools, so steady state allocates
+* device work of a tick: for each build, the upload of its weights from
+  pinned host memory and the build, on ``build_streams`` streams (table
+  objects come from pools reserved at start-up: a table of n weights takes
+  the smallest free object of capacity >= n, so the steady state allocates
   nothing), then ONE ``wrs_sample_many`` launch for all the tick's sample
   requests -- old and new tables alike -- and one device-to-host copy of the
   outputs; ticks overlap each other on the device;
@@ -65,10 +67,6 @@ class Request:
     build: bool         # carries the table's weights (else: sample a resident table)
 
 
-def table_weight_seed(table: int) -> int:
-    return 0x5EED0000 + 7919 * table
-
-
 def request_stream(nreq: int, rate: float, seed: int, build_frac: float = 0.3, n_lo: int = 1 << 10,
                    n_hi: int = 1 << 24, k_lo: int = 1, k_hi: int = 10 ** 5, recent: int = 64):
     """Seeded request stream: Poisson arrivals at `rate` per second; a request
@@ -101,18 +99,28 @@ def request_stream(nreq: int, rate: float, seed: int, build_frac: float = 0.3, n
     return reqs
 
 
+MAX_CLASS = 32
+
+
 class TableCache:
     """Resident tables in LRU order under a byte budget.  A table used by an
-    in-flight tick is pinned and never evicted.  Pool objects (free tables
-    kept for reuse, by capacity class) count against the budget too."""
+    in-flight tick is pinned and never evicted.  Table objects live on after
+    eviction in pools by capacity class (2^c); pooled objects count against
+    the budget too.  A table of class c takes the smallest pooled object of
+    class >= c; else a new object if the budget allows; else the object of
+    the least recently used unpinned table of class >= c; else pooled and
+    unpinned resident objects of smaller classes are freed until a new one
+    fits."""
 
     def __init__(self, budget: int):
         self.budget = budget
-        self.resident = collections.OrderedDict()  # table id -> (cls, obj)
+        self.resident = collections.OrderedDict()  # table id -> (cls of the object, obj)
         self.pins = collections.Counter()
         self.pool = collections.defaultdict(list)  # cls -> [obj]
         self.used = 0  # bytes of resident + pooled objects
         self.evictions = 0
+        self.created = 0
+        self.freed = 0
 
     def get(self, tid):
         e = self.resident.get(tid)
@@ -128,46 +136,85 @@ class TableCache:
         if self.pins[tid] <= 0:
             del self.pins[tid]
 
-    def acquire(self, cls: int, create, free):
-        """An object of class cls for a new resident table: from the pool,
-        else created within the budget (evicting unpinned LRU tables into the
-        pool, then freeing pooled objects of other classes).  None when the
-        budget cannot hold it now (the caller retries on a later tick)."""
+    def reserve(self, cls: int, create) -> bool:
+        """Create one pooled object of class cls if the budget allows."""
         need = table_bytes(1 << cls)
-        while True:
-            if self.pool[cls]:
-                return self.pool[cls].pop()
+        if self.used + need > self.budget:
+            return False
+        self.used += need
+        self.created += 1
+        self.pool[cls].append(create(1 << cls))
+        return True
+
+    def acquire(self, cls: int, create, free):
+        """(object, its class) for a new resident table of class cls, or None
+        when nothing can be had until in-flight ticks complete."""
+        for c in range(cls, MAX_CLASS + 1):
+            if self.pool.get(c):
+                return self.pool[c].pop(), c
+        need = table_bytes(1 << cls)
+        if self.used + need <= self.budget:
+            self.used += need
+            self.created += 1
+            return create(1 << cls), cls
+        for tid, (c, obj) in self.resident.items():  # least recently used first
+            if c >= cls and tid not in self.pins:
+                del self.resident[tid]
+                self.evictions += 1
+                return obj, c
+        # make room from smaller objects: pooled first, then unpinned residents (LRU)
+        smaller = [(c, o) for c in sorted(self.pool) if c < cls for o in self.pool[c]]
+        smaller += [(c, o, tid) for tid, (c, o) in self.resident.items() if c < cls and tid not in self.pins]
+        room = self.budget - self.used + sum(table_bytes(1 << e[0]) for e in smaller)
+        if room < need:
+            return None
+        for e in smaller:
             if self.used + need <= self.budget:
-                self.used += need
-                return create(1 << cls)
-            if not self._evict_one() and not self._free_pooled(cls, free):
-                return None
+                break
+            c, o = e[0], e[1]
+            if len(e) == 3:
+                del self.resident[e[2]]
+                self.evictions += 1
+            else:
+                self.pool[c].remove(o)
+            free(o)
+            self.freed += 1
+            self.used -= table_bytes(1 << c)
+        self.used += need
+        self.created += 1
+        return create(1 << cls), cls
 
     def insert(self, tid, cls, obj):
         self.resident[tid] = (cls, obj)
 
-    def _evict_one(self) -> bool:
-        for tid in self.resident:
-            if tid not in self.pins:
-                cls, obj = self.resident.pop(tid)
-                self.pool[cls].append(obj)
-                self.evictions += 1
-                return True
-        return False
-
-    def _free_pooled(self, keep_cls: int, free) -> bool:
-        for c in sorted(self.pool, reverse=True):
-            if c != keep_cls and self.pool[c]:
-                free(self.pool[c].pop())
-                self.used -= table_bytes(1 << c)
-                return True
-        return False
-
     def clear_resident(self):
-        """Return every resident table to the pool (between runs)."""
+        """Return every resident table's object to the pool (between runs)."""
         for tid, (cls, obj) in list(self.resident.items()):
             self.pool[cls].append(obj)
         self.resident.clear()
+
+
+class WeightSource:
+    """Request payloads: the weights of table t are the first n entries of one
+    of `variants` binary32 Zipf(1.0) arrays of 2^max_class weights (randomly
+    permuted ranks, workloads.f32_zipf's recipe made on the device), kept in
+    pinned host memory; a build uploads them like a client's payload."""
+
+    def __init__(self, torch, max_class: int = 24, variants: int = 4):
+        self.max_n = 1 << max_class
+        self.arrays = []
+        for v in range(variants):
+            d = WL.generate_device("f32_zipf", self.max_n, 0x5EED + v, 1.0)
+            h = torch.empty(self.max_n, dtype=torch.float32, pin_memory=True)
+            h.copy_(d)
+            self.arrays.append(h)
+        torch.cuda.synchronize()
+
+    def host(self, table: int, n: int):
+        """Pinned host tensor view of table `table`'s n weights."""
+        if n > self.max_n:
+            raise ValueError("table larger than the payload source")
+        return self.arrays[table % len(self.arrays)][:n]
 
 
 # ------------------------------------------------------------------ GPU side
@@ -190,12 +237,13 @@ class Server:
     """Continuous-batching server (see module docstring) on the current GPU."""
 
     def __init__(self, budget: int = 40 << 30, max_inflight: int = 3, tick_requests: int = 2048,
-                 tick_samples: int = 1 << 24, build_streams: int = 4):
+                 tick_samples: int = 1 << 24, build_streams: int = 4, payload: "WeightSource | None" = None):
         import torch
 
         from . import wrs
 
         self.torch, self.wrs = torch, wrs
+        self.payload = payload or WeightSource(torch)
         self.cache = TableCache(budget)
         self.max_inflight = max_inflight
         self.tick_requests = tick_requests
@@ -217,19 +265,39 @@ class Server:
         self.last_use.pop(id(t), None)
         t.free()
 
+    def reserve(self, reqs, fill: float = 0.9) -> int:
+        """Start-up: pool table objects for the size classes that `reqs` build,
+        in proportion to how often each class is built, filling `fill` of the
+        budget.  Returns the number of objects created."""
+        counts = collections.Counter(table_class(r.n) for r in reqs if r.build)
+        if not counts:
+            return 0
+        total = sum(counts.values())
+        unit = sum(m / total * table_bytes(1 << c) for c, m in counts.items())
+        units = fill * self.cache.budget / unit
+        made = 0
+        for c, m in sorted(counts.items()):
+            for _ in range(max(1, int(m / total * units))):
+                if not self.cache.reserve(c, self._create):
+                    break
+                made += 1
+        self.torch.cuda.synchronize()
+        return made
+
     def _build(self, req, stream):
-        """Weights of req's table generated on `stream` (the request's payload),
-        then its build; returns the table object or None (no memory now)."""
-        cls = table_class(req.n)
-        t = self.cache.acquire(cls, self._create, self._free)
-        if t is None:
+        """Upload req's table weights (its payload) on `stream` and build the
+        table there; returns (table object, staging buffer) or None when no
+        table object can be had now."""
+        r = self.cache.acquire(table_class(req.n), self._create, self._free)
+        if r is None:
             return None
+        t, cls = r
         ev = self.last_use.get(id(t))
         if ev is not None:
             stream.wait_event(ev)
         with self.torch.cuda.stream(stream):
-            w = WL.generate_device("f32_zipf", req.n, table_weight_seed(req.table), 1.0,
-                                   stream=stream.cuda_stream)
+            w = self.torch.empty(req.n, dtype=self.torch.float32, device="cuda")
+            w.copy_(self.payload.host(req.table, req.n), non_blocking=True)
             t.build(w, stream=stream.cuda_stream)
         self.cache.insert(req.table, cls, t)
         return t, w

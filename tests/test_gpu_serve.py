@@ -20,15 +20,21 @@ def _requests(nreq, seed, rate=20000.0):
     return S.request_stream(nreq, rate=rate, seed=seed, n_lo=1 << 10, n_hi=1 << 16, k_hi=5000)
 
 
-def _oracle_samples(r):
-    w = WL.generate_device("f32_zipf", r.n, S.table_weight_seed(r.table), 1.0).cpu().numpy()
+@pytest.fixture(scope="module")
+def payload():
+    return S.WeightSource(torch, max_class=16, variants=3)
+
+
+def _oracle_samples(r, payload):
+    w = payload.host(r.table, r.n).numpy().copy()
     _, tab = O.build_table(w)
     return O.sample(tab.thr, tab.alias, tab.Qp, r.k, r.seed & MASK64, r.stream_id)
 
 
-def test_served_equals_plain_and_oracle():
+def test_served_equals_plain_and_oracle(payload):
     reqs = _requests(400, 3)
-    srv = S.Server(budget=2 << 30, max_inflight=3, tick_requests=64, tick_samples=1 << 20)
+    srv = S.Server(budget=2 << 30, max_inflight=3, tick_requests=64, tick_samples=1 << 20, payload=payload)
+    assert srv.reserve(reqs, fill=0.1) > 0
     try:
         served = srv.run(reqs, keep_outputs=True)
         assert served["ticks"] > 3, "requests must be batched over several overlapping ticks"
@@ -39,13 +45,14 @@ def test_served_equals_plain_and_oracle():
     for r in reqs:
         assert np.array_equal(served["outputs"][r.rid], plain["outputs"][r.rid]), r
     for r in reqs[:25] + [r for r in reqs if not r.build][:15]:
-        assert np.array_equal(served["outputs"][r.rid], _oracle_samples(r)), r
+        assert np.array_equal(served["outputs"][r.rid], _oracle_samples(r, payload)), r
 
 
-def test_tiny_budget_evicts_and_rebuilds_same_results():
+def test_tiny_budget_evicts_and_rebuilds_same_results(payload):
     reqs = _requests(300, 8)
-    small = S.Server(budget=6 * S.table_bytes(1 << 16), max_inflight=2, tick_requests=8, tick_samples=1 << 18)
-    big = S.Server(budget=2 << 30, max_inflight=1, tick_requests=1, tick_samples=1 << 18)
+    small = S.Server(budget=6 * S.table_bytes(1 << 16), max_inflight=2, tick_requests=8, tick_samples=1 << 18,
+                     payload=payload)
+    big = S.Server(budget=2 << 30, max_inflight=1, tick_requests=1, tick_samples=1 << 18, payload=payload)
     try:
         a = small.run(reqs, keep_outputs=True)
         assert a["evictions"] > 10

@@ -48,31 +48,47 @@ def test_cache_lru_pins_and_budget():
         return o
 
     for tid in range(3):
-        o = c.acquire(10, create, freed.append)
-        assert o is not None
-        c.insert(tid, 10, o)
+        o, cls = c.acquire(10, create, freed.append)
+        assert cls == 10
+        c.insert(tid, cls, o)
     assert len(created) == 3 and c.used == 3 * one
     c.get(0)  # 0 becomes most recent: LRU order 1, 2, 0
     c.pin(1)
-    o = c.acquire(10, create, freed.append)  # evicts 2 (1 is pinned), reuses its object
-    assert o is not None and len(created) == 3 and 2 not in c.resident and c.evictions == 1
-    c.insert(3, 10, o)
+    o, cls = c.acquire(10, create, freed.append)  # takes 2's object (1 is pinned)
+    assert len(created) == 3 and 2 not in c.resident and c.evictions == 1
+    c.insert(3, cls, o)
     c.pin(0)
     c.pin(3)
     assert c.acquire(10, create, freed.append) is None  # everything pinned, budget full
     c.unpin(0)
-    assert c.acquire(10, create, freed.append) is not None  # 0 evicted now
-    assert 0 not in c.resident and 1 in c.resident and 3 in c.resident
+    assert c.acquire(10, create, freed.append) is not None  # 0's object now
+    assert 0 not in c.resident and 1 in c.resident and 3 in c.resident and not freed
 
 
-def test_cache_frees_pooled_objects_of_other_classes():
+def test_cache_serves_small_tables_from_larger_pooled_objects():
+    c = S.TableCache(budget=10 * S.table_bytes(1 << 14))
+    assert c.reserve(14, Obj) and c.reserve(12, Obj)
+    o, cls = c.acquire(11, Obj, None)  # smallest pooled class >= 11
+    assert cls == 12 and o.cap == 1 << 12
+    o, cls = c.acquire(11, Obj, None)
+    assert cls == 14
+    o, cls = c.acquire(11, Obj, None)  # pool empty: a new class-11 object within the budget
+    assert cls == 11 and c.created == 3
+
+
+def test_cache_frees_smaller_objects_for_a_large_table():
     small, big = S.table_bytes(1 << 10), S.table_bytes(1 << 12)
     c = S.TableCache(budget=2 * small + big - 1)
     freed = []
     for tid in range(2):
-        c.insert(tid, 10, c.acquire(10, Obj, freed.append))
-    # a class-12 table does not fit: both class-10 tables are evicted into the
-    # pool, then pooled objects are freed until it fits
-    o = c.acquire(12, Obj, freed.append)
-    assert o is not None and o.cap == 1 << 12
-    assert len(freed) >= 1 and c.used <= c.budget
+        o, cls = c.acquire(10, Obj, freed.append)
+        c.insert(tid, cls, o)
+    c.pin(1)
+    c.pin(0)
+    # no object of class >= 12 exists and both small tables are pinned
+    assert c.acquire(12, Obj, freed.append) is None
+    c.unpin(0)
+    # the unpinned small table is freed (the pinned one stays) and a class-12 object fits
+    o, cls = c.acquire(12, Obj, freed.append)
+    assert cls == 12 and len(freed) == 1 and 0 not in c.resident and 1 in c.resident
+    assert c.used <= c.budget and c.freed == 1
