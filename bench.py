@@ -222,7 +222,7 @@ def cpu_baseline(names, n_s: int):
 def config(args, names):
     return {"workload": f"n={args.n:.0e} binary32 weights ({', '.join(names)}; randomly permuted), "
                         f"table build + k={args.k:.0e} samples per step, steps cycle the distributions",
-            "n": args.n, "k": args.k, "dists": names, "tile": 4096,
+            "n": args.n, "k": args.k, "dists": names, "tile": 2048,
             "l2": "inputs larger than L2 (4 GB weights, 16 GB table vs 129 MB L2)",
             "parallelism": "replicas"}
 

@@ -65,19 +65,19 @@ __global__ void k_gather(const uint4 *__restrict__ tab, uint64_t n, uint64_t k, 
                          uint32_t *__restrict__ out)
 {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < k; s += 4 * stride) {
-        uint64_t r[4];
-        uint4 b[4];
+    for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < k; s += 8 * stride) {
+        uint64_t r[8];
+        uint4 b[8];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) r[j] = __umul64hi(splitmix64(seed + s + j * stride), n);
+        for (int j = 0; j < 8; ++j) r[j] = __umul64hi(splitmix64(seed + s + j * stride), n);
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
+        for (int j = 0; j < 8; ++j)
             if (s + j * stride < k)
                 asm volatile("ld.global.nc.L2::64B.v4.u32 {%0, %1, %2, %3}, [%4];"
                              : "=r"(b[j].x), "=r"(b[j].y), "=r"(b[j].z), "=r"(b[j].w)
                              : "l"(tab + r[j]));
 #pragma unroll
-        for (int j = 0; j < 4; ++j) if (s + j * stride < k) __stcs(out + s + j * stride, b[j].x ^ b[j].z);
+        for (int j = 0; j < 8; ++j) if (s + j * stride < k) __stcs(out + s + j * stride, b[j].x ^ b[j].z);
     }
 }
 
@@ -89,8 +89,8 @@ extern "C" int wl_random_gather(const void *d_table, uint64_t n, uint64_t k, uin
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    uint64_t want = (k + 1023) / 1024;
-    uint64_t cap = (uint64_t)(sms > 0 ? sms : 1) * 8;
+    uint64_t want = (k + 2047) / 2048;
+    uint64_t cap = (uint64_t)(sms > 0 ? sms : 1) * 16; // the sampler's launch shape
     unsigned blocks = (unsigned)(want < cap ? (want ? want : 1) : cap);
     k_gather<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(static_cast<const uint4 *>(d_table), n, k, seed,
                                                                     static_cast<uint32_t *>(d_out));

@@ -34,6 +34,8 @@ struct wrs_table {
     uint64_t stage_w_bytes;
     uint32_t *stage_out;   // host-API staging (samples)
     uint64_t stage_out_cap;
+    cudaStream_t copy_stream; // host-API: device-to-host copies overlapped with sampling
+    cudaEvent_t copy_ev;
     int host_status;       // last status read back (-1: unknown)
     cudaEvent_t ev[kStages + 1]; // stage timing (created when enabled)
     int timing;            // record ev[] around the build's kernels
@@ -157,6 +159,20 @@ wrs_status enqueue_build(wrs_table *t, const void *d_weights, uint64_t n, wrs_dt
     return st;
 }
 
+// Samples [s0, s1) of the table into d_out[s0 ...].
+wrs_status launch_sample(const wrs_table *t, uint64_t s0, uint64_t s1, uint64_t seed, uint64_t stream_id,
+                         uint32_t *d_out, cudaStream_t s)
+{
+    const int sms = sm_count();
+    const uint64_t k = s1 - s0;
+    uint64_t want = (k + 256ull * kSampleUnroll - 1) / (256ull * kSampleUnroll);
+    uint64_t cap = (uint64_t)sms * 16; // 16 blocks per SM: more random loads in flight
+    const uint32_t blocks = (uint32_t)(want < cap ? (want < 1 ? 1 : want) : cap);
+    k_sample<<<blocks, 256, 0, s>>>(t->buckets, t->n, t->hdr, s0, s1, (uint32_t)seed, (uint32_t)(seed >> 32),
+                                    (uint32_t)stream_id, (uint32_t)(stream_id >> 32), d_out);
+    return launch_err();
+}
+
 wrs_status read_status(const wrs_table *t, uint32_t *out)
 {
     cudaError_t e = cudaDeviceSynchronize();
@@ -230,14 +246,7 @@ wrs_status wrs_sample(const wrs_table *t, uint64_t k, uint64_t seed, uint64_t st
     if (k == 0) return WRS_OK;
     if (!d_out) return WRS_EINVAL;
     if (t->host_status > 0) return (wrs_status)t->host_status;
-    const int sms = sm_count();
-    uint64_t want = (k + 256ull * kSampleUnroll - 1) / (256ull * kSampleUnroll);
-    uint64_t cap = (uint64_t)sms * 8;
-    const uint32_t blocks = (uint32_t)(want < cap ? (want < 1 ? 1 : want) : cap);
-    k_sample<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(
-        t->buckets, t->n, t->hdr, k, (uint32_t)seed, (uint32_t)(seed >> 32), (uint32_t)stream_id,
-        (uint32_t)(stream_id >> 32), d_out);
-    return launch_err();
+    return launch_sample(t, 0, k, seed, stream_id, d_out, static_cast<cudaStream_t>(stream));
 }
 
 wrs_status wrs_table_build_host(wrs_table *t, const void *h_weights, uint64_t n, wrs_dtype dtype, void *stream)
@@ -263,16 +272,34 @@ wrs_status wrs_sample_host(wrs_table *t, uint64_t k, uint64_t seed, uint64_t str
     if (!t || t->n == 0) return WRS_EINVAL;
     if (k == 0) return WRS_OK;
     if (!h_out) return WRS_EINVAL;
+    if (t->host_status > 0) return (wrs_status)t->host_status;
     if (t->stage_out_cap < k) {
         if (t->stage_out) { cudaDeviceSynchronize(); cudaFree(t->stage_out); t->stage_out = nullptr; t->stage_out_cap = 0; }
         cudaError_t e = cudaMalloc(&t->stage_out, k * sizeof(uint32_t));
         if (e != cudaSuccess) return cuda_err(e);
         t->stage_out_cap = k;
     }
+    if (!t->copy_stream) {
+        cudaError_t e = cudaStreamCreateWithFlags(&t->copy_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t->copy_ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_err(e);
+    }
+    // sample in chunks; each chunk's copy to the host runs on copy_stream
+    // while the next chunk is drawn
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    wrs_status st = wrs_sample(t, k, seed, stream_id, t->stage_out, stream);
-    if (st != WRS_OK) return st;
-    cudaError_t e = cudaMemcpyAsync(h_out, t->stage_out, k * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    const uint64_t chunk = 1ull << 25;
+    for (uint64_t c0 = 0; c0 < k; c0 += chunk) {
+        const uint64_t c1 = c0 + chunk < k ? c0 + chunk : k;
+        wrs_status st = launch_sample(t, c0, c1, seed, stream_id, t->stage_out, s);
+        if (st != WRS_OK) return st;
+        cudaError_t e = cudaEventRecord(t->copy_ev, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(t->copy_stream, t->copy_ev, 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h_out + c0, t->stage_out + c0, (c1 - c0) * sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                                t->copy_stream);
+        if (e != cudaSuccess) return cuda_err(e);
+    }
+    cudaError_t e = cudaStreamSynchronize(t->copy_stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     return cuda_err(e);
 }
@@ -390,6 +417,8 @@ void wrs_table_free(wrs_table *t)
     cudaFree(t->buckets);
     if (t->stage_w) cudaFree(t->stage_w);
     if (t->stage_out) cudaFree(t->stage_out);
+    if (t->copy_stream) cudaStreamDestroy(t->copy_stream);
+    if (t->copy_ev) cudaEventDestroy(t->copy_ev);
     delete t;
 }
 

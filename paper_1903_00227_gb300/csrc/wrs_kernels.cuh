@@ -977,7 +977,7 @@ __device__ __forceinline__ uint4 ld_bucket(const uint4 *p)
     return v;
 }
 
-constexpr int kSampleUnroll = 4;
+constexpr int kSampleUnroll = 8;
 
 // Samples first, first + stride, ... (below k) of one table.
 __device__ __forceinline__ void sample_body(const uint4 *__restrict__ tab, uint64_t n, uint64_t qp, uint64_t k,
@@ -1012,14 +1012,15 @@ __device__ __forceinline__ void sample_body(const uint4 *__restrict__ tab, uint6
     }
 }
 
+// Samples [s0, k) of one table.
 __global__ void __launch_bounds__(256) k_sample(const uint4 *__restrict__ tab, uint64_t n,
-                                                const DevHeader *__restrict__ hdr, uint64_t k, uint32_t key0,
-                                                uint32_t key1, uint32_t sid0, uint32_t sid1,
+                                                const DevHeader *__restrict__ hdr, uint64_t s0, uint64_t k,
+                                                uint32_t key0, uint32_t key1, uint32_t sid0, uint32_t sid1,
                                                 uint32_t *__restrict__ out)
 {
     if (hdr->status) return;
-    sample_body(tab, n, hdr->qp, k, key0, key1, sid0, sid1, out, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
-                (uint64_t)gridDim.x * blockDim.x);
+    sample_body(tab, n, hdr->qp, k, key0, key1, sid0, sid1, out,
+                s0 + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, (uint64_t)gridDim.x * blockDim.x);
 }
 
 } // namespace wrs
