@@ -478,3 +478,134 @@ void wo_sample_at(uint64_t n, const uint64_t *thr, const uint32_t *al, uint64_t 
         out[t] = one;
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Two-level ("2lvl-sweep") tables, Sec. 6 "Distributed Alias Table          */
+/* Construction" with the replicated top level, and Sec. 10 "Implementation  */
+/* Details" (2lvl with Alg. 2 as the base case), applied recursively.        */
+/*                                                                            */
+/* Level 0 holds the n items in groups of G consecutive items (the last one  */
+/* may be shorter).  Each group gets its own Alg. 2 table over its members in */
+/* the group's own units: capacity Q_g = sum of its members' q, member m     */
+/* weighs n_g * q_m (n_g = members of the group).  The groups' totals are    */
+/* the items ("meta-items") of level 1, grouped the same way, and so on until */
+/* a level has a single group.  Buckets are encoded per group (s_g, qp_g as  */
+/* in wo_encode with Q_g); an alias is stored as the member's index within   */
+/* its level.                                                                 */
+/*                                                                            */
+/* Sampling walks down from the top group: at depth d (0 at the top) Philox  */
+/* with counter (s, stream) and key (seed_lo + d*0x9E3779B9, seed_hi +        */
+/* d*0xBB67AE85) gives u and v; r = floor(u*n_g / 2^64) picks a bucket of the */
+/* current group, the coin floor(v*qp_g / 2^64) < thr keeps r or takes the   */
+/* alias, and the pick names the group of the next level down.  The pick at  */
+/* level 0 is the sample.  With n <= G there is one level and one group, and */
+/* table and samples are exactly those of wo_sweep + wo_encode + wo_sample.  */
+/* ------------------------------------------------------------------------ */
+
+#define WO_MAX_LEVELS 16
+
+/* Entries per level: sizes[0] = n, sizes[l+1] = ceil(sizes[l] / G); returns L. */
+int wo_2lvl_levels(uint64_t n, uint64_t G, uint64_t *sizes)
+{
+    int L = 0;
+    uint64_t m = n;
+    if (n == 0 || G < 2) return 0;
+    for (;;) {
+        sizes[L++] = m;
+        if (m <= G || L == WO_MAX_LEVELS) break;
+        m = (m + G - 1) / G;
+    }
+    return L;
+}
+
+/* thr, al: sum of sizes entries (level 0 first); qp, shift, tot (two words  */
+/* each): one entry per group, level 0's groups first.                        */
+int wo_2lvl_build(uint64_t n, const uint64_t *q, uint64_t G, uint64_t *thr, uint32_t *al,
+                  uint64_t *qp, uint32_t *shift, uint64_t *tot)
+{
+    uint64_t sizes[WO_MAX_LEVELS];
+    int L = wo_2lvl_levels(n, G, sizes), l;
+    uint64_t off = 0, goff = 0;
+    const uint64_t *w = q;
+    uint64_t *bw, *next;
+    if (L == 0) return WO_EINVAL;
+    bw = (uint64_t *)malloc(2 * G * sizeof(uint64_t));
+    next = (uint64_t *)malloc(2 * ((n + G - 1) / G + 1) * sizeof(uint64_t));
+    if (!bw || !next) { free(bw); free(next); return WO_EINVAL; }
+    for (l = 0; l < L; ++l) {
+        const uint64_t N = sizes[l], ng_groups = (N + G - 1) / G;
+        uint64_t g;
+        for (g = 0; g < ng_groups; ++g) {
+            const uint64_t b0 = g * G, ng = (N - b0 < G) ? N - b0 : G;
+            uint64_t Qg[2], m, qpg;
+            uint32_t sg;
+            u128 S = 0;
+            int rc;
+            for (m = 0; m < ng; ++m) S += ld128(w + 2 * (b0 + m));
+            st128(Qg, S);
+            rc = wo_sweep(ng, w + 2 * b0, Qg, bw, al + off + b0);
+            if (rc) { free(bw); free(next); return rc; }
+            wo_encode(ng, bw, Qg, thr + off + b0, &qpg, &sg);
+            for (m = 0; m < ng; ++m) al[off + b0 + m] += (uint32_t)b0;
+            qp[goff + g] = qpg;
+            shift[goff + g] = sg;
+            st128(tot + 2 * (goff + g), S);
+            st128(next + 2 * g, S);
+        }
+        /* the group totals are the next level's weights */
+        if (l + 1 < L) {
+            uint64_t *cur = (uint64_t *)malloc(2 * ng_groups * sizeof(uint64_t));
+            if (!cur) { free(bw); free(next); return WO_EINVAL; }
+            memcpy(cur, next, 2 * ng_groups * sizeof(uint64_t));
+            if (w != q) free((void *)w);
+            w = cur;
+        }
+        off += N;
+        goff += ng_groups;
+    }
+    if (w != q) free((void *)w);
+    free(bw);
+    free(next);
+    return WO_OK;
+}
+
+static uint32_t sample_2lvl_one(int L, const uint64_t *sizes, uint64_t G, const uint64_t *thr,
+                                const uint32_t *al, const uint64_t *qp, uint64_t seed, uint64_t stream, uint64_t s)
+{
+    uint64_t offs[WO_MAX_LEVELS], goffs[WO_MAX_LEVELS], o = 0, go = 0, g = 0;
+    int l, d;
+    for (l = 0; l < L; ++l) { offs[l] = o; goffs[l] = go; o += sizes[l]; go += (sizes[l] + G - 1) / G; }
+    for (d = 0; d < L; ++d) {
+        const int lv = L - 1 - d;
+        const uint64_t base = g * G, ng = (sizes[lv] - base < G) ? sizes[lv] - base : G;
+        uint32_t key[2], ctr[4], x[4];
+        uint64_t u, v, r, b;
+        key[0] = (uint32_t)seed + (uint32_t)d * 0x9E3779B9u;
+        key[1] = (uint32_t)(seed >> 32) + (uint32_t)d * 0xBB67AE85u;
+        ctr[0] = (uint32_t)s; ctr[1] = (uint32_t)(s >> 32);
+        ctr[2] = (uint32_t)stream; ctr[3] = (uint32_t)(stream >> 32);
+        wo_philox4x32_10(ctr, key, x);
+        u = (uint64_t)x[0] | ((uint64_t)x[1] << 32);
+        v = (uint64_t)x[2] | ((uint64_t)x[3] << 32);
+        r = (uint64_t)(((u128)u * ng) >> 64);
+        b = offs[lv] + base + r;
+        g = ((uint64_t)(((u128)v * qp[goffs[lv] + g]) >> 64) < thr[b]) ? base + r : al[b];
+    }
+    return (uint32_t)g;
+}
+
+void wo_2lvl_sample(uint64_t n, uint64_t G, const uint64_t *thr, const uint32_t *al, const uint64_t *qp,
+                    uint64_t k, uint64_t seed, uint64_t stream, uint32_t *out)
+{
+    uint64_t sizes[WO_MAX_LEVELS], s;
+    int L = wo_2lvl_levels(n, G, sizes);
+    for (s = 0; s < k; ++s) out[s] = sample_2lvl_one(L, sizes, G, thr, al, qp, seed, stream, s);
+}
+
+void wo_2lvl_sample_at(uint64_t n, uint64_t G, const uint64_t *thr, const uint32_t *al, const uint64_t *qp,
+                       uint64_t seed, uint64_t stream, const uint64_t *s_idx, uint64_t m, uint32_t *out)
+{
+    uint64_t sizes[WO_MAX_LEVELS], t;
+    int L = wo_2lvl_levels(n, G, sizes);
+    for (t = 0; t < m; ++t) out[t] = sample_2lvl_one(L, sizes, G, thr, al, qp, seed, stream, s_idx[t]);
+}

@@ -77,6 +77,14 @@ def lib():
             L.wo_sample.restype = None
             L.wo_sample_at.argtypes = [U64, P, P, U64, U64, U64, P, U64, P]
             L.wo_sample_at.restype = None
+            L.wo_2lvl_levels.argtypes = [U64, U64, P]
+            L.wo_2lvl_levels.restype = INT
+            L.wo_2lvl_build.argtypes = [U64, P, U64, P, P, P, P, P]
+            L.wo_2lvl_build.restype = INT
+            L.wo_2lvl_sample.argtypes = [U64, U64, P, P, P, U64, U64, U64, P]
+            L.wo_2lvl_sample.restype = None
+            L.wo_2lvl_sample_at.argtypes = [U64, U64, P, P, P, U64, U64, P, U64, P]
+            L.wo_2lvl_sample_at.restype = None
             _lib = L
     return _lib
 
@@ -94,7 +102,8 @@ class use_library:
         self.saved = _lib
         L = ctypes.CDLL(self.path)
         for name in ("wo_quantize", "wo_sweep", "wo_vose", "wo_psa", "wo_vose_f64", "wo_encode",
-                     "wo_philox4x32_10", "wo_sample", "wo_sample_at"):
+                     "wo_philox4x32_10", "wo_sample", "wo_sample_at", "wo_2lvl_levels", "wo_2lvl_build",
+                     "wo_2lvl_sample", "wo_2lvl_sample_at"):
             f, g = getattr(L, name), getattr(self.saved, name)
             f.argtypes, f.restype = g.argtypes, g.restype
         with _lock:
@@ -251,4 +260,66 @@ def sample_at(thr: np.ndarray, alias: np.ndarray, Qp: int, seed: int, stream: in
     idx = np.ascontiguousarray(idx, dtype=np.uint64)
     out = np.zeros(max(idx.shape[0], 1), dtype=np.uint32)
     lib().wo_sample_at(thr.shape[0], _ptr(thr), _ptr(alias), Qp, seed, stream, _ptr(idx), idx.shape[0], _ptr(out))
+    return out[: idx.shape[0]]
+
+
+# ------------------------------------------------- two-level ("2lvl-sweep") tables
+GROUP = 2048  # members per group at every level
+
+
+class TwoLevel:
+    """Multi-level table (Sec. 6, replicated top level, Alg. 2 per group):
+    per level, thresholds and aliases (alias = member index within the level);
+    per group (level 0's groups first), qp, shift and the exact group total."""
+
+    def __init__(self, n: int, G: int, sizes, thr, alias, qp, shift, tot):
+        self.n, self.G, self.sizes = n, G, list(sizes)
+        self.thr, self.alias, self.qp, self.shift, self.tot = thr, alias, qp, shift, tot
+
+    @property
+    def levels(self) -> int:
+        return len(self.sizes)
+
+    def level_slice(self, level: int) -> slice:
+        o = sum(self.sizes[:level])
+        return slice(o, o + self.sizes[level])
+
+    def group_slice(self, level: int) -> slice:
+        o = sum((m + self.G - 1) // self.G for m in self.sizes[:level])
+        return slice(o, o + (self.sizes[level] + self.G - 1) // self.G)
+
+
+def levels_2lvl(n: int, G: int = GROUP):
+    sizes = np.zeros(16, dtype=np.uint64)
+    L = lib().wo_2lvl_levels(n, G, _ptr(sizes))
+    return [int(x) for x in sizes[:L]]
+
+
+def build_2lvl(qz: Quantized, G: int = GROUP) -> TwoLevel:
+    n = qz.n
+    sizes = levels_2lvl(n, G)
+    total = sum(sizes)
+    groups = sum((m + G - 1) // G for m in sizes)
+    thr = np.zeros(total, dtype=np.uint64)
+    al = np.zeros(total, dtype=np.uint32)
+    qp = np.zeros(groups, dtype=np.uint64)
+    sh = np.zeros(groups, dtype=np.uint32)
+    tot = np.zeros((groups, 2), dtype=np.uint64)
+    rc = lib().wo_2lvl_build(n, _ptr(qz.q), G, _ptr(thr), _ptr(al), _ptr(qp), _ptr(sh), _ptr(tot))
+    if rc:
+        raise OracleError(rc, "2lvl_build")
+    return TwoLevel(n, G, sizes, thr, al, qp, sh, tot)
+
+
+def sample_2lvl(t: TwoLevel, k: int, seed: int, stream: int = 0) -> np.ndarray:
+    out = np.zeros(max(k, 1), dtype=np.uint32)
+    lib().wo_2lvl_sample(t.n, t.G, _ptr(t.thr), _ptr(t.alias), _ptr(t.qp), k, seed, stream, _ptr(out))
+    return out[:k]
+
+
+def sample_2lvl_at(t: TwoLevel, seed: int, stream: int, idx: np.ndarray) -> np.ndarray:
+    idx = np.ascontiguousarray(idx, dtype=np.uint64)
+    out = np.zeros(max(idx.shape[0], 1), dtype=np.uint32)
+    lib().wo_2lvl_sample_at(t.n, t.G, _ptr(t.thr), _ptr(t.alias), _ptr(t.qp), seed, stream, _ptr(idx),
+                            idx.shape[0], _ptr(out))
     return out[: idx.shape[0]]
