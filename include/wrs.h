@@ -300,6 +300,54 @@ const void *wrs_table_device_header(const wrs_table *t);
 const void *wrs_batch_device_header(const wrs_batch *b, uint32_t table);
 
 /*
+ * Two-level ("2lvl-sweep") tables: Sec. 6 "Distributed Alias Table
+ * Construction" with the replicated top level, and Sec. 10 "Implementation
+ * Details" (2lvl with Alg. 2 as the base case), applied recursively on one GPU.
+ *
+ * The items are cut into groups of WRS_TABLE2_GROUP consecutive items; each
+ * group gets its own Alg. 2 table in the group's units (capacity Q_g = the
+ * group's exact total, member m weighs n_g * q_m, n_g = members of the group;
+ * buckets encoded as wrs_bucket with the group's shift and qp); the group
+ * totals are the items of the next level, up to one group (at most three
+ * levels for n < 2^32).  An alias is the member's index within its level.
+ * Sample s walks down from the top group: at depth d (0 at the top), Philox
+ * with counter (s, stream_id) and key (seed_lo + d * 0x9E3779B9, seed_hi +
+ * d * 0xBB67AE85) gives u, v; r = floor(u * n_g / 2^64) picks a bucket of the
+ * current group, heads iff floor(v * qp_g / 2^64) < thr keeps r, else the
+ * alias; the pick is the group one level down, and at level 0 the sample.
+ * With n <= WRS_TABLE2_GROUP the table and the samples are exactly those of
+ * wrs_table_build and wrs_sample.  Each item is drawn with probability
+ * w_i / W up to the same per-level discretisation as the single table.
+ * It is a different table from wrs_table_build's for larger n, built in two
+ * passes over the weights (exact total, then one block per group) with no
+ * global prefix or split search.
+ *
+ * Arguments, ownership, streams and errors as for the wrs_table_* calls.
+ */
+#define WRS_TABLE2_GROUP 2048
+#define WRS_TABLE2_MAX_LEVELS 4
+typedef struct wrs_table2 wrs_table2;
+typedef struct {
+    uint64_t qp;        /* Q_g >> shift: the group's coin denominator */
+    uint32_t shift;     /* max(0, bitlen(Q_g) - 64) */
+    uint32_t members;   /* n_g */
+} wrs_group;
+
+wrs_status wrs_table2_create(uint64_t capacity_n, wrs_table2 **out);
+wrs_status wrs_table2_build(wrs_table2 *t, const void *d_weights, uint64_t n, wrs_dtype dtype, void *stream);
+wrs_status wrs_table2_sample(const wrs_table2 *t, uint64_t k, uint64_t seed, uint64_t stream_id,
+                             uint32_t *d_out, void *stream);
+/* Synchronise; the build's status (device-detected errors as wrs_table_status). */
+wrs_status wrs_table2_status(const wrs_table2 *t);
+/* Levels of the last build and their sizes (h_sizes: WRS_TABLE2_MAX_LEVELS entries, may be NULL). */
+wrs_status wrs_table2_layout(const wrs_table2 *t, uint32_t *h_levels, uint64_t *h_sizes);
+/* Synchronise and copy the buckets of all levels (level 0 first, 16 B each)
+ * and the group records (level 0's groups first); either pointer may be NULL. */
+wrs_status wrs_table2_download(const wrs_table2 *t, void *h_buckets, uint64_t bucket_bytes,
+                               void *h_groups, uint64_t group_bytes);
+void wrs_table2_free(wrs_table2 *t);
+
+/*
  * Build without allocating (no counterpart in the paper).
  *
  * For callers that cannot call cudaMalloc -- code running inside a CUDA graph

@@ -20,7 +20,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared"]
 
 TARGETS = {
-    "libwrs.so": (["wrs.cu"], ["wrs_device.cuh", "wrs_kernels.cuh", "wrs_batch.cuh"], [os.path.join(INCLUDE, "wrs.h")]),
+    "libwrs.so": (["wrs.cu"], ["wrs_device.cuh", "wrs_kernels.cuh", "wrs_batch.cuh", "wrs_twolevel.cuh"], [os.path.join(INCLUDE, "wrs.h")]),
     "libwrs_workloads.so": (["workloads.cu"], [], []),
 }
 

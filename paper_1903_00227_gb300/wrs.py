@@ -90,6 +90,13 @@ _sig = {
     "wrs_sample_many": ([_P, ctypes.c_uint32, _U64, _P, _P], _I),
     "wrs_table_device_header": ([_TBL], _P),
     "wrs_batch_device_header": ([_TBL, ctypes.c_uint32], _P),
+    "wrs_table2_create": ([_U64, _PTBL], _I),
+    "wrs_table2_build": ([_TBL, _P, _U64, _I, _P], _I),
+    "wrs_table2_sample": ([_TBL, _U64, _U64, _U64, _P, _P], _I),
+    "wrs_table2_status": ([_TBL], _I),
+    "wrs_table2_layout": ([_TBL, _P, _P], _I),
+    "wrs_table2_download": ([_TBL, _P, _U64, _P, _U64], _I),
+    "wrs_table2_free": ([_TBL], None),
 }
 for _name, (_args, _res) in _sig.items():
     _f = getattr(_lib, _name)
@@ -484,3 +491,109 @@ class AliasBatch:
         except Exception:
             pass
 
+
+TABLE2_GROUP = 2048
+TABLE2_MAX_LEVELS = 4
+
+
+def table2_create(capacity_n: int):
+    h = ctypes.c_void_p()
+    rc = _lib.wrs_table2_create(capacity_n, ctypes.byref(h))
+    return rc, h.value
+
+
+def table2_build(t, d_weights: int, n: int, dtype: int, stream: int = 0) -> int:
+    return _lib.wrs_table2_build(t, d_weights, n, dtype, stream)
+
+
+def table2_sample(t, k: int, seed: int, stream_id: int, d_out: int, stream: int = 0) -> int:
+    return _lib.wrs_table2_sample(t, k, seed, stream_id, d_out, stream)
+
+
+def table2_status(t) -> int:
+    return _lib.wrs_table2_status(t)
+
+
+def table2_layout(t):
+    L = ctypes.c_uint32()
+    sizes = (ctypes.c_uint64 * TABLE2_MAX_LEVELS)()
+    rc = _lib.wrs_table2_layout(t, ctypes.byref(L), sizes)
+    return rc, [int(sizes[i]) for i in range(L.value)]
+
+
+def table2_download(t, h_buckets: int, bucket_bytes: int, h_groups: int, group_bytes: int) -> int:
+    return _lib.wrs_table2_download(t, h_buckets, bucket_bytes, h_groups, group_bytes)
+
+
+def table2_free(t) -> None:
+    _lib.wrs_table2_free(t)
+
+
+class AliasTable2:
+    """Owns one two-level ("2lvl-sweep") table (``wrs_table2``)."""
+
+    def __init__(self, capacity_n: int):
+        rc, h = table2_create(capacity_n)
+        _check(rc, "wrs_table2_create")
+        self.handle = h
+        self.capacity = capacity_n
+        self.n = 0
+
+    def build(self, weights, stream=None) -> "AliasTable2":
+        assert weights.is_cuda and weights.is_contiguous()
+        n = weights.numel()
+        _check(table2_build(self.handle, weights.data_ptr(), n, _dtype_code(weights), _stream_handle(stream)),
+               "wrs_table2_build")
+        self.n = n
+        return self
+
+    def sample(self, k: int, seed: int, stream_id: int = 0, out=None, stream=None):
+        import torch
+
+        if out is None:
+            out = torch.empty(max(k, 1), dtype=torch.int32, device="cuda")
+        assert out.is_cuda and out.is_contiguous() and out.numel() >= k and out.element_size() == 4
+        _check(table2_sample(self.handle, k, seed, stream_id, out.data_ptr(), _stream_handle(stream)),
+               "wrs_table2_sample")
+        return out
+
+    def status(self) -> int:
+        return table2_status(self.handle)
+
+    def levels(self):
+        rc, sizes = table2_layout(self.handle)
+        _check(rc, "wrs_table2_layout")
+        return sizes
+
+    def download(self):
+        """(thr, alias) over all levels (level 0 first) and per group (qp, shift, members)."""
+        import numpy as np
+
+        sizes = self.levels()
+        nb = sum(sizes)
+        ng = sum((m + TABLE2_GROUP - 1) // TABLE2_GROUP for m in sizes)
+        buf = np.empty(nb * 2, dtype=np.uint64)
+        grp = np.empty(ng * 2, dtype=np.uint64)
+        _check(table2_download(self.handle, buf.ctypes.data, buf.nbytes, grp.ctypes.data, grp.nbytes),
+               "wrs_table2_download")
+        words = buf.view(np.uint32).reshape(nb, 4)
+        gw = grp.view(np.uint32).reshape(ng, 4)
+        return (buf.reshape(nb, 2)[:, 0].copy(), words[:, 2].copy(), words[:, 3].copy(),
+                grp.reshape(ng, 2)[:, 0].copy(), gw[:, 2].copy(), gw[:, 3].copy())
+
+    def free(self) -> None:
+        if self.handle:
+            table2_free(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.free()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
