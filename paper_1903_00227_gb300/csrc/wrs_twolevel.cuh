@@ -47,11 +47,11 @@ struct Walk {              // the levels in the sampler's order: depth 0 = the t
 };
 
 struct GroupSmem {
-    u128 okey[kTile];       // keys D of the group's lights, in order (swizzled)
-    u128 hkey[kTile];       // keys E of the group's heavies (swizzled)
+    u128 okey[kTile];       // keys D of the group's lights, in order (swizzled; u64 keys use the front half)
+    u128 hkey[kTile];       // keys E of the group's heavies
     uint16_t ooff[kTile];   // their offsets in the group
     uint16_t hoff[kTile];
-    U2 scan[kWarps];
+    U2 scan[kWarps];        // pair scan (u128 pairs, or u64 pairs at the front)
     u128 red[kWarps];
     uint32_t cnt[kWarps];
 };
@@ -69,7 +69,160 @@ __device__ __forceinline__ u128 block_sum128(u128 v, u128 *sm)
     return t;
 }
 
-// One group of level `level` per block.  SRC 0: u32 words, 1: binary32 words
+// Keys of width K in shared memory: u128 (8 per 128-B bank row) or u64 (16
+// per row); the column is XORed with the row's low bits so that threads
+// reading rows at a fixed stride hit distinct banks.
+template <typename K> __device__ __forceinline__ uint32_t swzk(uint32_t j);
+template <> __device__ __forceinline__ uint32_t swzk<u128>(uint32_t j) { return j ^ ((j >> 3) & 7u); }
+template <> __device__ __forceinline__ uint32_t swzk<uint64_t>(uint32_t j) { return j ^ ((j >> 4) & 15u); }
+
+template <typename K> __device__ __forceinline__ K shfl_up_k(K v, int d);
+template <> __device__ __forceinline__ u128 shfl_up_k<u128>(u128 v, int d) { return shfl_up128(v, d); }
+template <> __device__ __forceinline__ uint64_t shfl_up_k<uint64_t>(uint64_t v, int d)
+{
+    return __shfl_up_sync(0xFFFFFFFFu, v, d);
+}
+
+template <typename K> struct PairK { K a, b; };
+
+// Exclusive block scan of two values per thread; total = the block's sums.
+template <typename K>
+__device__ __forceinline__ PairK<K> block_exclusive_scan_pair(PairK<K> v, PairK<K> &total, PairK<K> *sm)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    PairK<K> inc = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const K a = shfl_up_k<K>(inc.a, d), b = shfl_up_k<K>(inc.b, d);
+        if (lane >= d) { inc.a += a; inc.b += b; }
+    }
+    if (lane == 31) sm[wid] = inc;
+    __syncthreads();
+    PairK<K> base{0, 0};
+    for (int i = 0; i < wid; ++i) { base.a += sm[i].a; base.b += sm[i].b; }
+    total = PairK<K>{0, 0};
+#pragma unroll
+    for (int i = 0; i < kWarps; ++i) { total.a += sm[i].a; total.b += sm[i].b; }
+    PairK<K> r;
+    r.a = base.a + inc.a - v.a;
+    r.b = base.b + inc.b - v.b;
+    return r;
+}
+
+template <typename K> __device__ __forceinline__ uint64_t thr_of(K bw, uint32_t shift);
+template <> __device__ __forceinline__ uint64_t thr_of<u128>(u128 bw, uint32_t shift) { return lo64(bw >> shift); }
+template <> __device__ __forceinline__ uint64_t thr_of<uint64_t>(uint64_t bw, uint32_t) { return bw; }
+
+// Alg. 2 on one group with keys of width K (u64 when n_g * Q_g < 2^63): the
+// group's lights get exclusive prefix keys D of their deficits Q_g - n_g q,
+// its heavies inclusive prefix keys E of their excesses n_g q - Q_g, and the
+// two sequences are merged (heavy first when E <= D) over the threads.
+template <typename K>
+__device__ __forceinline__ bool group_build(GroupSmem &S, const u128 (&q)[kItems], u128 Qg128, uint32_t ng,
+                                            uint64_t N, uint64_t first, uint64_t base, uint32_t shift,
+                                            uint4 *__restrict__ buckets)
+{
+    K *okey = reinterpret_cast<K *>(S.okey);
+    K *hkey = reinterpret_cast<K *>(S.hkey);
+    PairK<K> *sm = reinterpret_cast<PairK<K> *>(S.scan);
+    const K Qg = (K)Qg128;
+    uint32_t lmask = 0, hmask = 0;
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+        if (first + k < N) {
+            if ((K)q[k] * (K)ng <= Qg) lmask |= 1u << k; else hmask |= 1u << k;
+        }
+    }
+    uint32_t tot;
+    const uint32_t ex = block_exclusive_scan_u32((uint32_t)__popc(lmask) | ((uint32_t)__popc(hmask) << 16), tot,
+                                                 S.cnt); // syncs: key arrays free
+    const uint32_t nl = tot & 0xFFFFu, nh = tot >> 16;
+    K sd = 0, se = 0;
+    {
+        uint32_t ls = ex & 0xFFFFu, hs = ex >> 16;
+#pragma unroll
+        for (int k = 0; k < kItems; ++k) {
+            const K nq = (K)q[k] * (K)ng;
+            const uint16_t off = (uint16_t)(threadIdx.x * kItems + k);
+            if ((lmask >> k) & 1u) {
+                const K d = Qg - nq; // deficit
+                okey[swzk<K>(ls)] = d;
+                S.ooff[ls] = off;
+                sd += d;
+                ++ls;
+            } else if ((hmask >> k) & 1u) {
+                const K e = nq - Qg; // excess
+                hkey[swzk<K>(hs)] = e;
+                S.hoff[hs] = off;
+                se += e;
+                ++hs;
+            }
+        }
+    }
+    PairK<K> sums;
+    const PairK<K> exs = block_exclusive_scan_pair<K>(PairK<K>{sd, se}, sums, sm);
+    {   // deficits -> exclusive prefix D, excesses -> inclusive prefix E, in place
+        const uint32_t l0 = ex & 0xFFFFu, h0 = ex >> 16;
+        K kl = exs.a, ke = exs.b;
+        for (uint32_t j = 0; j < (uint32_t)__popc(lmask); ++j) {
+            const K d = okey[swzk<K>(l0 + j)];
+            okey[swzk<K>(l0 + j)] = kl;
+            kl += d;
+        }
+        for (uint32_t j = 0; j < (uint32_t)__popc(hmask); ++j) {
+            ke += hkey[swzk<K>(h0 + j)];
+            hkey[swzk<K>(h0 + j)] = ke;
+        }
+    }
+    const K D_end = sums.a; // total deficit (= total excess)
+    __syncthreads();
+
+    bool bad = sums.a != sums.b;
+    const uint32_t M = ng;
+    const uint32_t per = (M + kThreads - 1) / kThreads;
+    const uint32_t d0 = threadIdx.x * per;
+    if (d0 < M) {
+        uint32_t lo = d0 > nl ? d0 - nl : 0, hi = d0 < nh ? d0 : nh;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi + 1) >> 1; // is heavy mid-1 before light d0-mid?
+            if (hkey[swzk<K>(mid - 1)] <= okey[swzk<K>(d0 - mid)]) lo = mid; else hi = mid - 1;
+        }
+        uint32_t j = lo, i = d0 - lo;
+        const uint32_t steps = min(per, M - d0);
+        K ej = j < nh ? hkey[swzk<K>(j)] : (K)0;
+        K di = i < nl ? okey[swzk<K>(i)] : D_end;
+        for (uint32_t st = 0; st < steps; ++st) {
+            if ((j < nh) && (i >= nl || ej <= di)) { // heavy j: bucket Q_g - (D_i - E_j), alias the next heavy
+                const K gap = di - ej;
+                if (gap > Qg) bad = true;
+                const uint32_t me = (uint32_t)(base + S.hoff[j]);
+                const uint32_t nx = j + 1 < nh ? (uint32_t)(base + S.hoff[j + 1]) : kNone;
+                if (nx == kNone && gap != 0) bad = true;
+                const uint32_t alias = (nx == kNone || gap == 0) ? me : nx;
+                const uint64_t thr = thr_of<K>(Qg - gap, shift);
+                buckets[me] = make_uint4((uint32_t)thr, (uint32_t)(thr >> 32), alias, 0u);
+                ++j;
+                if (j < nh) ej = hkey[swzk<K>(j)];
+            } else { // light i: its own weight, alias the current heavy (itself when full)
+                const K dn = i + 1 < nl ? okey[swzk<K>(i + 1)] : D_end;
+                const K nq = Qg - (dn - di);
+                const uint32_t me = (uint32_t)(base + S.ooff[i]);
+                uint32_t alias = me;
+                if (nq != Qg) {
+                    if (j < nh) alias = (uint32_t)(base + S.hoff[j]);
+                    else bad = true;
+                }
+                const uint64_t thr = thr_of<K>(nq, shift);
+                buckets[me] = make_uint4((uint32_t)thr, (uint32_t)(thr >> 32), alias, 0u);
+                ++i;
+                di = dn;
+            }
+        }
+    }
+    return bad;
+}
+
+// One group of a level per block.  SRC 0: u32 words, 1: binary32 words
 // (both level 0), 2: exact 128-bit member weights (two words, levels >= 1).
 template <int SRC>
 __global__ void __launch_bounds__(kThreads, 3) k2_group(const void *__restrict__ src, uint64_t N, int vec,
@@ -102,9 +255,8 @@ __global__ void __launch_bounds__(kThreads, 3) k2_group(const void *__restrict__
 #pragma unroll
     for (int k = 0; k < kItems; ++k) part += q[k];
     const u128 Qg = block_sum128(part, S.red); // the group's capacity
-    int sh = bitlen128(Qg) - 64;
-    if (sh < 0) sh = 0;
-    const uint32_t shift = (uint32_t)sh;
+    const int bits = bitlen128(Qg);
+    const uint32_t shift = bits > 64 ? (uint32_t)(bits - 64) : 0u;
     if (threadIdx.x == 0) {
         GroupRec r;
         r.qp = lo64(Qg >> shift);
@@ -113,103 +265,10 @@ __global__ void __launch_bounds__(kThreads, 3) k2_group(const void *__restrict__
         groups[blockIdx.x] = r;
         if (meta) { meta[2 * blockIdx.x] = lo64(Qg); meta[2 * blockIdx.x + 1] = hi64(Qg); }
     }
-
-    // classification (light iff n_g * q <= Q_g) and the two class counts
-    uint32_t lmask = 0, hmask = 0;
-#pragma unroll
-    for (int k = 0; k < kItems; ++k) {
-        if (first + k < N) {
-            if (q[k] * (u128)ng <= Qg) lmask |= 1u << k; else hmask |= 1u << k;
-        }
-    }
-    uint32_t tot;
-    const uint32_t ex = block_exclusive_scan_u32((uint32_t)__popc(lmask) | ((uint32_t)__popc(hmask) << 16), tot,
-                                                 S.cnt); // syncs: key arrays free
-    const uint32_t nl = tot & 0xFFFFu, nh = tot >> 16;
-    u128 sd = 0, se = 0;
-    {
-        uint32_t ls = ex & 0xFFFFu, hs = ex >> 16;
-#pragma unroll
-        for (int k = 0; k < kItems; ++k) {
-            const u128 nq = q[k] * (u128)ng;
-            const uint16_t off = (uint16_t)(threadIdx.x * kItems + k);
-            if ((lmask >> k) & 1u) {
-                const u128 d = Qg - nq; // deficit
-                S.okey[swz(ls)] = d;
-                S.ooff[ls] = off;
-                sd += d;
-                ++ls;
-            } else if ((hmask >> k) & 1u) {
-                const u128 e = nq - Qg; // excess
-                S.hkey[swz(hs)] = e;
-                S.hoff[hs] = off;
-                se += e;
-                ++hs;
-            }
-        }
-    }
-    U2 sums;
-    const U2 exs = block_exclusive_scan2(U2{sd, se}, sums, S.scan);
-    {   // deficits -> exclusive prefix D, excesses -> inclusive prefix E, in place
-        const uint32_t l0 = ex & 0xFFFFu, h0 = ex >> 16;
-        u128 kl = exs.a, ke = exs.b;
-        for (uint32_t j = 0; j < (uint32_t)__popc(lmask); ++j) {
-            const u128 d = S.okey[swz(l0 + j)];
-            S.okey[swz(l0 + j)] = kl;
-            kl += d;
-        }
-        for (uint32_t j = 0; j < (uint32_t)__popc(hmask); ++j) {
-            ke += S.hkey[swz(h0 + j)];
-            S.hkey[swz(h0 + j)] = ke;
-        }
-    }
-    const u128 D_end = sums.a; // total deficit (= total excess)
-    __syncthreads();
-
-    // merge of the lights (keys D) and the heavies (keys E), heavy first when
-    // E <= D, split evenly over the threads by merge-path co-ranks
-    bool bad = sums.a != sums.b;
-    const uint32_t M = ng;
-    const uint32_t per = (M + kThreads - 1) / kThreads;
-    const uint32_t d0 = threadIdx.x * per;
-    if (d0 < M) {
-        uint32_t lo = d0 > nl ? d0 - nl : 0, hi = d0 < nh ? d0 : nh;
-        while (lo < hi) {
-            const uint32_t mid = (lo + hi + 1) >> 1; // is heavy mid-1 before light d0-mid?
-            if (S.hkey[swz(mid - 1)] <= S.okey[swz(d0 - mid)]) lo = mid; else hi = mid - 1;
-        }
-        uint32_t j = lo, i = d0 - lo;
-        const uint32_t steps = min(per, M - d0);
-        u128 ej = j < nh ? S.hkey[swz(j)] : (u128)0;
-        u128 di = i < nl ? S.okey[swz(i)] : D_end;
-        for (uint32_t st = 0; st < steps; ++st) {
-            if ((j < nh) && (i >= nl || ej <= di)) { // heavy j: bucket Q_g - (D_i - E_j), alias the next heavy
-                const u128 gap = di - ej;
-                if (gap > Qg) bad = true;
-                const uint32_t me = (uint32_t)(base + S.hoff[j]);
-                const uint32_t nx = j + 1 < nh ? (uint32_t)(base + S.hoff[j + 1]) : kNone;
-                if (nx == kNone && gap != 0) bad = true;
-                const uint32_t alias = (nx == kNone || gap == 0) ? me : nx;
-                const uint64_t thr = lo64((Qg - gap) >> shift);
-                buckets[me] = make_uint4((uint32_t)thr, (uint32_t)(thr >> 32), alias, 0u);
-                ++j;
-                if (j < nh) ej = S.hkey[swz(j)];
-            } else { // light i: its own weight, alias the current heavy (itself when full)
-                const u128 dn = i + 1 < nl ? S.okey[swz(i + 1)] : D_end;
-                const u128 nq = Qg - (dn - di);
-                const uint32_t me = (uint32_t)(base + S.ooff[i]);
-                uint32_t alias = me;
-                if (nq != Qg) {
-                    if (j < nh) alias = (uint32_t)(base + S.hoff[j]);
-                    else bad = true;
-                }
-                const uint64_t thr = lo64(nq >> shift);
-                buckets[me] = make_uint4((uint32_t)thr, (uint32_t)(thr >> 32), alias, 0u);
-                ++i;
-                di = dn;
-            }
-        }
-    }
+    // n_g <= 2^11, so every scaled quantity and key is below n_g * Q_g < 2^63
+    // when Q_g < 2^52: 64-bit arithmetic is exact (the common case)
+    const bool bad = bits <= 52 ? group_build<uint64_t>(S, q, Qg, ng, N, first, base, shift, buckets)
+                                : group_build<u128>(S, q, Qg, ng, N, first, base, shift, buckets);
     if (bad) set_status(hdr, kEInternal);
 }
 
