@@ -65,6 +65,7 @@ def parse():
                     help="weights (and samples) per distribution for the CPU-oracle baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--no-two-level", action="store_true")
     ap.add_argument("--batch-tables", type=int, default=4096,
                     help="tables of the many-distribution workload (0: skip it)")
     ap.add_argument("--batch-steps", type=int, default=10)
@@ -254,6 +255,54 @@ def run_reference(args, names):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+TWO_LEVEL_BYTES_PER_WEIGHT = 20  # two 4-B weight reads + 12-B payload (upper levels: < 0.1%)
+
+
+def run_two_level(args, torch, wrs, weights, names, stream, peak):
+    """The two-level ("2lvl-sweep") table on the same inputs: build and k
+    samples per distribution, CUDA events on the launching stream."""
+    n, k = args.n, args.k
+    sh = stream.cuda_stream
+    t2 = wrs.AliasTable2(n)
+    out = torch.empty(k, dtype=torch.int32, device="cuda")
+    per = {}
+    for name in names:
+        w = weights[name]
+        for _ in range(2):
+            t2.build(w, stream=sh)
+            t2.sample(k, 1, out=out, stream=sh)
+        torch.cuda.synchronize()
+        bt, st = [], []
+        for i in range(max(3, args.steps // 2)):
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            t2.build(w, stream=sh)
+            e1.record(stream)
+            t2.sample(k, 100 + i, out=out, stream=sh)
+            e2.record(stream)
+            e2.synchronize()
+            bt.append(e0.elapsed_time(e1))
+            st.append(e1.elapsed_time(e2))
+        if t2.status() != wrs.OK:
+            raise RuntimeError("two-level build failed")
+        bm, sm_ = statistics.mean(bt), statistics.mean(st)
+        per[name] = {"build_ms": bm, "build_gweights_s": n / (bm * 1e-3) / 1e9,
+                     "build_frac": TWO_LEVEL_BYTES_PER_WEIGHT * n / (bm * 1e-3) / 1e9 / peak,
+                     "sample_ms": sm_, "sample_gsamples_s": k / (sm_ * 1e-3) / 1e9}
+    levels = t2.levels()
+    t2.free()
+    bmean = statistics.mean(v["build_ms"] for v in per.values())
+    smean = statistics.mean(v["sample_ms"] for v in per.values())
+    return {"build_gweights_s": n / (bmean * 1e-3) / 1e9, "sample_gsamples_s": k / (smean * 1e-3) / 1e9,
+            "roofline_build": {"bound": "hbm", "achieved": TWO_LEVEL_BYTES_PER_WEIGHT * n / (bmean * 1e-3) / 1e9,
+                               "peak": peak, "unit": "GB/s",
+                               "frac": TWO_LEVEL_BYTES_PER_WEIGHT * n / (bmean * 1e-3) / 1e9 / peak,
+                               "algorithmic_bytes_per_weight": TWO_LEVEL_BYTES_PER_WEIGHT},
+            "levels": levels, "per_dist": per,
+            "note": "wrs_table2_*: Alg. 2 per group of 2048, group totals as the next level (Sec. 6); "
+                    "a different table from the headline's PSA table, same sampling distribution"}
 
 
 def run_batched(args, torch, WL, wrs, stream):
@@ -516,6 +565,10 @@ def run_ours(args, names):
                "d2h_bytes_per_step": 4 * k, "ms_per_step": t_e2e,
                "note": "wrs_table_build_host (H2D of the weights) + wrs_sample_host (D2H of the samples)"}
 
+    two_level = None
+    if not args.no_two_level:
+        two_level = run_two_level(args, torch, wrs, weights, names, stream, peak)
+
     batched = None
     if args.batch_tables > 0:
         batched = run_batched(args, torch, WL, wrs, stream)
@@ -542,7 +595,7 @@ def run_ours(args, names):
                                "frac": ach_build / peak, "algorithmic_bytes_per_weight": BUILD_BYTES_PER_WEIGHT,
                                "peak_source": peak_kind},
             "kernels": per_kernel, "per_dist": per_dist,
-            "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "many_tables": batched, "serving": serving,
+            "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "two_level": two_level, "many_tables": batched, "serving": serving,
             "gpu_launches": K * (len(wrs.STAGES) + 1),
             "context": {"paper_psa_build_gweights_s_n1e9": 0.99, "paper_psa_query_gsamples_s_n1e9": 1.662,
                         "paper_hardware": "4x Xeon Gold 6138, 158 threads (context only)"},
