@@ -86,7 +86,8 @@ def measured_peaks():
 
 def source_sha() -> str:
     h = hashlib.sha256()
-    for rel in ("paper_1903_00227_gb300/csrc/wrs_kernels.cuh", "paper_1903_00227_gb300/csrc/wrs_device.cuh"):
+    for rel in ("paper_1903_00227_gb300/csrc/wrs_kernels.cuh", "paper_1903_00227_gb300/csrc/wrs_device.cuh",
+                "paper_1903_00227_gb300/csrc/wrs_twolevel.cuh"):
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -94,7 +95,8 @@ def source_sha() -> str:
 
 def traffic_for(stage: str, units: int):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source; else None."""
+    on the current kernel source; else None.  `stage` is a build stage or a
+    kernel name."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -102,7 +104,7 @@ def traffic_for(stage: str, units: int):
         d = json.load(f)
     if d.get("source_sha") != source_sha():
         return None
-    e = d.get("kernels", {}).get(KERNEL_NAMES[stage])
+    e = d.get("kernels", {}).get(KERNEL_NAMES.get(stage, stage))
     if not e:
         return None
     return float(e["dram_bytes_per_unit"]) * units
@@ -297,7 +299,7 @@ def run_two_level(args, torch, wrs, weights, names, stream, peak):
     smean = statistics.mean(v["sample_ms"] for v in per.values())
     return {"build_gweights_s": n / (bmean * 1e-3) / 1e9, "sample_gsamples_s": k / (smean * 1e-3) / 1e9,
             "roofline_build": {"bound": "hbm", "achieved": TWO_LEVEL_BYTES_PER_WEIGHT * n / (bmean * 1e-3) / 1e9,
-                               "peak": peak, "unit": "GB/s",
+                               "peak": peak, "unit": "GB/s", "traffic_k2_group": traffic_for("k2_group", n),
                                "frac": TWO_LEVEL_BYTES_PER_WEIGHT * n / (bmean * 1e-3) / 1e9 / peak,
                                "algorithmic_bytes_per_weight": TWO_LEVEL_BYTES_PER_WEIGHT},
             "levels": levels, "per_dist": per,
