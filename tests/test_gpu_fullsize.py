@@ -67,3 +67,82 @@ def test_full_size_table_and_samples():
     want = O.sample_at(thr_h, alias_h, info.qp, 99, 3, pick.cpu().numpy().astype(np.uint64))
     assert np.array_equal(got, want)
     table.free()
+
+
+def test_full_size_two_level():
+    """The two-level table of the same 10^9 weights: every level-0 group is an
+    alias table of its members (exact mass identity on the GPU, all groups),
+    300 sampled groups and the whole upper levels equal the oracle's tables,
+    and 10^5 of 10^9 samples equal the oracle's walk on the same table."""
+    w = WL.generate_device("f32_uniform", N, 7)
+    t2 = wrs.AliasTable2(N)
+    t2.build(w)
+    assert t2.status() == wrs.OK
+    sizes = t2.levels()
+    G = wrs.TABLE2_GROUP
+    assert sizes[0] == N and all(sizes[i + 1] == -(-sizes[i] // G) for i in range(len(sizes) - 1))
+    nb, ng = sum(sizes), sum(-(-m // G) for m in sizes)
+    host = np.empty(2 * nb, dtype=np.uint64)
+    grp = np.empty(2 * ng, dtype=np.uint64)
+    assert wrs.table2_download(t2.handle, host.ctypes.data, host.nbytes, grp.ctypes.data, grp.nbytes) == wrs.OK
+    thr_all = host.reshape(nb, 2)[:, 0]
+    word1 = host.reshape(nb, 2)[:, 1]
+    alias_all = (word1 & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+    assert not (word1 >> np.uint64(32)).any()
+    qp_all = grp.reshape(ng, 2)[:, 0]
+    sh_all = (grp.reshape(ng, 2)[:, 1] & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+    g0 = -(-N // G)
+    # exact q: the uniform recipe's weights are k * 2^-24, k in [1, 2^24]
+    q = (w.double() * 2.0 ** 24).long()
+    assert bool((q >= 1).all()) and bool((q <= 2 ** 24).all())
+    pad = g0 * G - N
+    qg = torch.cat([q, torch.zeros(pad, dtype=torch.long, device="cuda")]).view(g0, G)
+    totals = qg.sum(dim=1)  # exact: < 2^35
+    assert np.array_equal(qp_all[:g0], totals.cpu().numpy().astype(np.uint64)) and not sh_all[:g0].any()
+    # every level-0 group: light buckets hold their weight, pieces add up to n_g * q
+    thr = torch.from_numpy(thr_all[:N].view(np.int64)).cuda()
+    alias = torch.from_numpy(alias_all[:N].astype(np.int64)).cuda()
+    idx = torch.arange(N, device="cuda")
+    gid = idx // G
+    ngm = torch.full((g0,), G, dtype=torch.long, device="cuda")
+    ngm[-1] = N - (g0 - 1) * G
+    nq = q * ngm[gid]
+    qpb = totals[gid]
+    assert bool((gid[alias] == gid).all()), "an alias leaves its group"
+    light = nq <= qpb
+    assert torch.equal(thr[light], nq[light])
+    other = alias != idx
+    assert bool((~light[alias[other]]).all())
+    mass = thr.clone()
+    mass.scatter_add_(0, alias[other], qpb[other] - thr[other])
+    assert torch.equal(mass, nq)
+    del thr, alias, idx, gid, nq, qpb, light, other, mass
+    # 300 sampled level-0 groups (and the ragged last one) against the oracle's Alg. 2
+    gen = np.random.default_rng(17)
+    qh = q.cpu().numpy()
+    for g in list(gen.choice(g0 - 1, 300, replace=False)) + [g0 - 1]:
+        b0, m = g * G, min(G, N - g * G)
+        qq = np.zeros((m, 2), np.uint64)
+        qq[:, 0] = qh[b0:b0 + m].astype(np.uint64)
+        Qg = int(qh[b0:b0 + m].sum())
+        tab = O.sweep(O.Quantized(qq, np.array([Qg, 0], np.uint64), 0))
+        assert np.array_equal(thr_all[b0:b0 + m], tab.thr), g
+        assert np.array_equal(alias_all[b0:b0 + m].astype(np.int64) - b0, tab.alias.astype(np.int64)), g
+    # the upper levels: the oracle's two-level table over the group totals
+    tq = np.zeros((g0, 2), np.uint64)
+    tq[:, 0] = totals.cpu().numpy().astype(np.uint64)
+    upper = O.build_2lvl(O.Quantized(tq, np.array([int(tq[:, 0].sum()), 0], np.uint64), 0))
+    assert upper.sizes == sizes[1:]
+    assert np.array_equal(thr_all[N:], upper.thr) and np.array_equal(alias_all[N:], upper.alias)
+    assert np.array_equal(qp_all[g0:], upper.qp) and np.array_equal(sh_all[g0:], upper.shift)
+    del q, qg, qh
+    # 10^9 samples; 10^5 of them walked by the oracle on the downloaded table
+    k = 10 ** 9
+    out = t2.sample(k, seed=99, stream_id=3)
+    pick = torch.randint(0, k, (100_000,), device="cuda", generator=torch.Generator(device="cuda").manual_seed(6))
+    got = out[pick].cpu().numpy().view(np.uint32)
+    walk = O.TwoLevel(N, G, sizes, np.ascontiguousarray(thr_all), np.ascontiguousarray(alias_all),
+                      np.ascontiguousarray(qp_all), sh_all, None)
+    want = O.sample_2lvl_at(walk, 99, 3, pick.cpu().numpy().astype(np.uint64))
+    assert np.array_equal(got, want)
+    t2.free()
