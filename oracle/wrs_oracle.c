@@ -36,6 +36,7 @@
 #include <stdlib.h>
 #include <string.h>
 #include <limits.h>
+#include <math.h>
 
 typedef unsigned __int128 u128;
 
@@ -609,3 +610,308 @@ void wo_2lvl_sample_at(uint64_t n, uint64_t G, const uint64_t *thr, const uint32
     int L = wo_2lvl_levels(n, G, sizes);
     for (t = 0; t < m; ++t) out[t] = sample_2lvl_one(L, sizes, G, thr, al, qp, seed, stream, s_idx[t]);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Output-sensitive sampling with replacement, OS-ND variant (Sec. 5         */
+/* "Output Sensitive Sampling With Replacement"; Sec. 10 "Optimizations":    */
+/* descent aborted for fewer than 128 samples from at least half as many     */
+/* items, no deduplication).  Reading: the divide-and-conquer tree is the    */
+/* two-level structure above -- within a group a complete binary tree over   */
+/* its members (node [a, b) splits at a + (b - a) / 2), whose leaves are     */
+/* either items (level 0) or the groups one level down.  A node with c       */
+/* samples gives Binomial(c, W_left / W_node) to its left child.  A group    */
+/* receiving c < 128 samples with 2 n_g >= c draws them as c queries of its  */
+/* alias table instead (level 0: one (item, 1) pair per query, duplicates    */
+/* kept; higher levels: the picks are counted per member).                   */
+/*                                                                            */
+/* Random bits: Philox4x32-10 with key seed and counter (g, h | level << 12  */
+/* | j << 14, stream) where g is the group, h the node's heap index (root 1, */
+/* children 2h and 2h + 1; 0 for the alias queries), j the draw's index.    */
+/* Binomial deviates: inversion when c * p < 10, else Hoermann's BTRS        */
+/* (transformed rejection with squeeze, 1993), both with p <= 1/2 by          */
+/* symmetry; log and exp are evaluated here from their series with basic     */
+/* IEEE binary64 operations only (compile without contraction), so any      */
+/* implementation that follows the same steps gets the same deviates.       */
+/* ------------------------------------------------------------------------ */
+
+static double det_ldexp(double x, int e)
+{
+    while (e > 1000) { x *= 0x1p1000; e -= 1000; }
+    while (e < -1000) { x *= 0x1p-1000; e += 1000; }
+    {
+        union { uint64_t u; double d; } t;
+        t.u = (uint64_t)(e + 1023) << 52;
+        return x * t.d;
+    }
+}
+
+/* nearest binary64 to the integer x (ties to even) */
+static double det_u128_to_double(u128 x)
+{
+    int b = bitlen128(x), sh;
+    u128 m, rem, half;
+    if (b <= 53) return (double)(uint64_t)x;
+    sh = b - 53;
+    m = x >> sh;
+    rem = x & (((u128)1 << sh) - 1);
+    half = (u128)1 << (sh - 1);
+    if (rem > half || (rem == half && (m & 1))) {
+        m += 1;
+        if (m >> 53) { m >>= 1; sh += 1; }
+    }
+    return det_ldexp((double)(uint64_t)m, sh);
+}
+
+/* natural logarithm of x > 0: x = f 2^e with f in [sqrt(1/2), sqrt(2)),   */
+/* log f = 2 atanh(s), s = (f - 1) / (f + 1), |s| < 0.172, series to s^25  */
+static double det_log(double x)
+{
+    union { uint64_t u; double d; } t;
+    int e;
+    double f, s, s2, acc;
+    int k;
+    t.d = x;
+    e = (int)((t.u >> 52) & 0x7FF);
+    if (e == 0) { /* subnormal: scale up first */
+        t.d = x * 0x1p64;
+        e = (int)((t.u >> 52) & 0x7FF) - 64;
+    }
+    e -= 1023;
+    t.u = (t.u & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull;
+    f = t.d;
+    if (f > 1.4142135623730951) { f = f * 0.5; e += 1; }
+    s = (f - 1.0) / (f + 1.0);
+    s2 = s * s;
+    acc = 1.0 / 25.0;
+    for (k = 11; k >= 0; --k) acc = acc * s2 + 1.0 / (double)(2 * k + 1);
+    return (double)e * 0.6931471805599453 + 2.0 * s * acc;
+}
+
+/* e^x: x = k ln2 + r, |r| <= ln2 / 2 (+ rounding), Taylor to r^20 */
+static double det_exp(double x)
+{
+    double kd, r, acc;
+    int k, j;
+    if (x < -745.0) return 0.0;
+    kd = floor(x / 0.6931471805599453 + 0.5);
+    k = (int)kd;
+    r = x - kd * 0.6931471805599453;
+    acc = 1.0;
+    for (j = 20; j >= 1; --j) acc = acc * r / (double)j + 1.0;
+    return det_ldexp(acc, k);
+}
+
+typedef struct {
+    uint32_t key[2], ctr[4];
+    uint32_t j;      /* next Philox call of this node */
+    uint32_t buf[4];
+    int have;        /* uniforms left in buf (0..2) */
+} os_rng;
+
+static void os_rng_init(os_rng *r, uint64_t seed, uint64_t stream, uint32_t g, uint32_t h, uint32_t level)
+{
+    r->key[0] = (uint32_t)seed; r->key[1] = (uint32_t)(seed >> 32);
+    r->ctr[0] = g; r->ctr[1] = h | (level << 12);
+    r->ctr[2] = (uint32_t)stream; r->ctr[3] = (uint32_t)(stream >> 32);
+    r->j = 0;
+    r->have = 0;
+}
+
+/* uniform in [0, 1): the top 53 bits of a 64-bit word */
+static double os_unif(os_rng *r)
+{
+    uint64_t w;
+    if (r->have == 0) {
+        uint32_t c[4];
+        c[0] = r->ctr[0]; c[1] = r->ctr[1] | (r->j << 14); c[2] = r->ctr[2]; c[3] = r->ctr[3];
+        wo_philox4x32_10(c, r->key, r->buf);
+        r->j++;
+        r->have = 2;
+    }
+    w = r->have == 2 ? ((uint64_t)r->buf[0] | ((uint64_t)r->buf[1] << 32))
+                     : ((uint64_t)r->buf[2] | ((uint64_t)r->buf[3] << 32));
+    r->have--;
+    return (double)(w >> 11) * 0x1p-53;
+}
+
+/* log(k!) : exact product and det_log below 10, Stirling's series above */
+static double det_lfact(uint64_t k)
+{
+    if (k < 10) {
+        double f = 1.0;
+        uint64_t i;
+        for (i = 2; i <= k; ++i) f *= (double)i;
+        return det_log(f);
+    } else {
+        double z = (double)k + 1.0, z2 = z * z;
+        double corr = (1.0 / 12.0 - (1.0 / 360.0 - (1.0 / 1260.0 - (1.0 / 1680.0) / z2) / z2) / z2) / z;
+        return ((double)k + 0.5) * det_log(z) - z + 0.5 * det_log(6.283185307179586) + corr;
+    }
+}
+
+#define OS_MAX_DRAWS (1u << 18)
+
+/* Binomial(n, p) with p = num / den, 0 < num < den; p <= 1/2 by symmetry */
+static uint64_t os_binomial(uint64_t n, u128 num, u128 den, os_rng *rng)
+{
+    int flip = 0;
+    double p, q;
+    uint64_t x;
+    if (2 * num > den) { num = den - num; flip = 1; }
+    p = det_u128_to_double(num) / det_u128_to_double(den);
+    q = 1.0 - p;
+    if ((double)n * p < 10.0) { /* inversion */
+        const double s = p / q, a = ((double)n + 1.0) * s, r0 = det_exp((double)n * det_log(q));
+        for (;;) {
+            double u = os_unif(rng), r = r0;
+            x = 0;
+            while (u > r) {
+                u -= r;
+                x++;
+                if (x > n) break;
+                r *= a / (double)x - s;
+            }
+            if (x <= n) break;
+            if (rng->j >= OS_MAX_DRAWS) { x = (uint64_t)((double)n * p); break; }
+        }
+    } else { /* BTRS */
+        const double spq = sqrt((double)n * p * q);
+        const double b = 1.15 + 2.53 * spq, a = -0.0873 + 0.0248 * b + 0.01 * p, c = (double)n * p + 0.5;
+        const double vr = 0.92 - 4.2 / b, alpha = (2.83 + 5.1 / b) * spq, lpq = det_log(p / q);
+        const uint64_t m = (uint64_t)floor(((double)n + 1.0) * p);
+        const double h = det_lfact(m) + det_lfact(n - m);
+        for (;;) {
+            double u = os_unif(rng) - 0.5, v = os_unif(rng), us = 0.5 - fabs(u), kd;
+            if (rng->j >= OS_MAX_DRAWS) { x = m; break; }
+            kd = floor((2.0 * a / us + b) * u + c);
+            if (kd < 0.0 || kd > (double)n) continue;
+            x = (uint64_t)kd;
+            if (us >= 0.07 && v <= vr) break;
+            v = det_log(v * alpha / (a / (us * us) + b));
+            if (v <= h - det_lfact(x) - det_lfact(n - x) + ((double)x - (double)m) * lpq) break;
+        }
+    }
+    return flip ? n - x : x;
+}
+
+typedef struct {
+    int L;
+    uint64_t sizes[WO_MAX_LEVELS], offs[WO_MAX_LEVELS], goffs[WO_MAX_LEVELS];
+    uint64_t G;
+    const uint64_t *q, *tot, *thr, *qp;
+    const uint32_t *al;
+    uint64_t seed, stream;
+    uint32_t *out_item;
+    uint64_t *out_count;
+    uint64_t cap, nout;
+    int overflow;
+} os_ctx;
+
+/* exact weight of member m of level `level` */
+static u128 os_w(const os_ctx *x, int level, uint64_t m)
+{
+    return level == 0 ? ld128(x->q + 2 * m) : ld128(x->tot + 2 * (x->goffs[level - 1] + m));
+}
+
+static void os_emit(os_ctx *x, uint64_t item, uint64_t c)
+{
+    if (x->nout >= x->cap) { x->overflow = 1; return; }
+    x->out_item[x->nout] = (uint32_t)item;
+    x->out_count[x->nout] = c;
+    x->nout++;
+}
+
+static void os_group(os_ctx *x, int level, uint64_t g, uint64_t c);
+
+static void os_leaf(os_ctx *x, int level, uint64_t member, uint64_t c)
+{
+    if (level == 0) os_emit(x, member, c);
+    else os_group(x, level - 1, member, c);
+}
+
+static void os_node(os_ctx *x, int level, uint64_t g, uint64_t base, uint64_t a, uint64_t b, uint64_t h, uint64_t c)
+{
+    uint64_t mid, i, cl;
+    u128 wl = 0, wn = 0;
+    if (c == 0) return;
+    if (b - a == 1) { os_leaf(x, level, base + a, c); return; }
+    mid = a + (b - a) / 2;
+    for (i = a; i < b; ++i) {
+        const u128 w = os_w(x, level, base + i);
+        wn += w;
+        if (i < mid) wl += w;
+    }
+    if (wl == 0) cl = 0;
+    else if (wl == wn) cl = c;
+    else {
+        os_rng r;
+        os_rng_init(&r, x->seed, x->stream, (uint32_t)g, (uint32_t)h, (uint32_t)level);
+        cl = os_binomial(c, wl, wn, &r);
+    }
+    os_node(x, level, g, base, a, mid, 2 * h, cl);
+    os_node(x, level, g, base, mid, b, 2 * h + 1, c - cl);
+}
+
+static void os_group(os_ctx *x, int level, uint64_t g, uint64_t c)
+{
+    const uint64_t base = g * x->G, N = x->sizes[level];
+    const uint64_t ng = (N - base < x->G) ? N - base : x->G;
+    if (c == 0) return;
+    if (c < 128 && 2 * ng >= c) { /* OS-ND base case: c alias queries */
+        uint64_t picks[128], cnt[128], np = 0, t, s;
+        for (t = 0; t < c; ++t) {
+            uint32_t ctr[4], key[2], o[4];
+            uint64_t u, v, r, bkt, pick;
+            key[0] = (uint32_t)x->seed; key[1] = (uint32_t)(x->seed >> 32);
+            ctr[0] = (uint32_t)g; ctr[1] = ((uint32_t)level << 12) | ((uint32_t)t << 14);
+            ctr[2] = (uint32_t)x->stream; ctr[3] = (uint32_t)(x->stream >> 32);
+            wo_philox4x32_10(ctr, key, o);
+            u = (uint64_t)o[0] | ((uint64_t)o[1] << 32);
+            v = (uint64_t)o[2] | ((uint64_t)o[3] << 32);
+            r = (uint64_t)(((u128)u * ng) >> 64);
+            bkt = x->offs[level] + base + r;
+            pick = ((uint64_t)(((u128)v * x->qp[x->goffs[level] + g]) >> 64) < x->thr[bkt]) ? base + r : x->al[bkt];
+            if (level == 0) { os_emit(x, pick, 1); continue; }
+            for (s = 0; s < np && picks[s] != pick; ++s) {}
+            if (s == np) { picks[np] = pick; cnt[np] = 0; np++; }
+            cnt[s]++;
+        }
+        /* higher levels: each picked member once, with its count, in pick order */
+        for (s = 0; s < np; ++s) os_group(x, level - 1, picks[s], cnt[s]);
+        return;
+    }
+    os_node(x, level, g, base, 0, ng, 1, c);
+}
+
+/* Writes up to cap (item, count) pairs; returns the number written, or      */
+/* ~0 when cap was too small.  The table is wo_2lvl_build's output plus the  */
+/* items' exact weights q.                                                    */
+uint64_t wo_os_nd(uint64_t n, uint64_t G, const uint64_t *q, const uint64_t *thr, const uint32_t *al,
+                  const uint64_t *qp, const uint64_t *tot, uint64_t k, uint64_t seed, uint64_t stream,
+                  uint32_t *out_item, uint64_t *out_count, uint64_t cap)
+{
+    os_ctx x;
+    int l;
+    uint64_t o = 0, go = 0;
+    memset(&x, 0, sizeof(x));
+    x.L = wo_2lvl_levels(n, G, x.sizes);
+    for (l = 0; l < x.L; ++l) { x.offs[l] = o; x.goffs[l] = go; o += x.sizes[l]; go += (x.sizes[l] + G - 1) / G; }
+    x.G = G; x.q = q; x.tot = tot; x.thr = thr; x.qp = qp; x.al = al;
+    x.seed = seed; x.stream = stream;
+    x.out_item = out_item; x.out_count = out_count; x.cap = cap;
+    os_group(&x, x.L - 1, 0, k);
+    return x.overflow ? ~(uint64_t)0 : x.nout;
+}
+
+/* One deviate, for the distribution tests of the binomial generator. */
+uint64_t wo_binomial(uint64_t n, uint64_t num, uint64_t den, uint64_t seed, uint64_t node)
+{
+    os_rng r;
+    os_rng_init(&r, seed, 0, (uint32_t)node, (uint32_t)(node >> 32) & 0xFFFu, 0);
+    if (num == 0) return 0;
+    if (num >= den) return n;
+    return os_binomial(n, num, den, &r);
+}
+
+double wo_det_log(double x) { return det_log(x); }
+double wo_det_exp(double x) { return det_exp(x); }

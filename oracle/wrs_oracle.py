@@ -47,7 +47,7 @@ def build(force: bool = False) -> str:
     """Compile the oracle with gcc into ``oracle/libwrs_oracle.so``."""
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
         tmp = LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-o", tmp, SRC])
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-shared", "-fPIC", "-o", tmp, SRC, "-lm"])
         os.replace(tmp, LIB)
     return LIB
 
@@ -85,6 +85,14 @@ def lib():
             L.wo_2lvl_sample.restype = None
             L.wo_2lvl_sample_at.argtypes = [U64, U64, P, P, P, U64, U64, P, U64, P]
             L.wo_2lvl_sample_at.restype = None
+            L.wo_os_nd.argtypes = [U64, U64, P, P, P, P, P, U64, U64, U64, P, P, U64]
+            L.wo_os_nd.restype = U64
+            L.wo_binomial.argtypes = [U64, U64, U64, U64, U64]
+            L.wo_binomial.restype = U64
+            L.wo_det_log.argtypes = [ctypes.c_double]
+            L.wo_det_log.restype = ctypes.c_double
+            L.wo_det_exp.argtypes = [ctypes.c_double]
+            L.wo_det_exp.restype = ctypes.c_double
             _lib = L
     return _lib
 
@@ -103,7 +111,8 @@ class use_library:
         L = ctypes.CDLL(self.path)
         for name in ("wo_quantize", "wo_sweep", "wo_vose", "wo_psa", "wo_vose_f64", "wo_encode",
                      "wo_philox4x32_10", "wo_sample", "wo_sample_at", "wo_2lvl_levels", "wo_2lvl_build",
-                     "wo_2lvl_sample", "wo_2lvl_sample_at"):
+                     "wo_2lvl_sample", "wo_2lvl_sample_at", "wo_os_nd", "wo_binomial", "wo_det_log",
+                     "wo_det_exp"):
             f, g = getattr(L, name), getattr(self.saved, name)
             f.argtypes, f.restype = g.argtypes, g.restype
         with _lock:
@@ -323,3 +332,31 @@ def sample_2lvl_at(t: TwoLevel, seed: int, stream: int, idx: np.ndarray) -> np.n
     lib().wo_2lvl_sample_at(t.n, t.G, _ptr(t.thr), _ptr(t.alias), _ptr(t.qp), seed, stream, _ptr(idx),
                             idx.shape[0], _ptr(out))
     return out[: idx.shape[0]]
+
+
+# ------------------------------------------------- output-sensitive sampling (OS-ND)
+def os_nd(qz: Quantized, t: TwoLevel, k: int, seed: int, stream: int = 0, cap: int | None = None):
+    """(items, counts) of OS-ND sampling k items with replacement over the
+    two-level table t of the exact weights qz (pairs in the order drawn)."""
+    if cap is None:
+        cap = min(k, qz.n + 128 * (qz.n // t.G + 1)) + 1
+    items = np.zeros(max(cap, 1), dtype=np.uint32)
+    counts = np.zeros(max(cap, 1), dtype=np.uint64)
+    m = lib().wo_os_nd(qz.n, t.G, _ptr(qz.q), _ptr(t.thr), _ptr(t.alias), _ptr(t.qp), _ptr(t.tot), k, seed,
+                       stream, _ptr(items), _ptr(counts), cap)
+    if m == 2 ** 64 - 1:
+        raise OracleError(-1, "os_nd (output capacity)")
+    return items[:m], counts[:m]
+
+
+def binomial(n: int, num: int, den: int, seed: int, node: int) -> int:
+    """One Binomial(n, num/den) deviate of the OS-ND generator (node = draw stream)."""
+    return int(lib().wo_binomial(n, num, den, seed, node))
+
+
+def det_log(x: float) -> float:
+    return float(lib().wo_det_log(x))
+
+
+def det_exp(x: float) -> float:
+    return float(lib().wo_det_exp(x))
