@@ -347,6 +347,32 @@ wrs_status wrs_table2_download(const wrs_table2 *t, void *h_buckets, uint64_t bu
                                void *h_groups, uint64_t group_bytes);
 void wrs_table2_free(wrs_table2 *t);
 
+/* Output-sensitive sampling with replacement, OS-ND variant (Sec. 5 "Output
+ * Sensitive Sampling With Replacement"; Sec. 10 "Optimizations": descent
+ * aborted for fewer than 128 samples from at least half as many items, no
+ * deduplication), over a built two-level table.  Draws k samples and writes
+ * them as (item, count) pairs: every item reached by the divide-and-conquer
+ * descent once with its count, and one (item, 1) pair per alias query of the
+ * base case, in no particular order; the counts add up to k.  Within a group
+ * a binary tree over its members (node [a, b) splits at a + (b - a) / 2)
+ * gives Binomial(c, W_left / W_node) of a node's c samples to its left
+ * child; a group receiving c < 128 samples from at least c/2 members draws
+ * them as alias queries.  Random bits: Philox4x32-10, key seed, counter (g,
+ * h | level << 12 | j << 14, stream_id) with g the group, h the node's heap
+ * index (root 1; 0 for alias queries) and j the draw.  Binomial deviates:
+ * inversion when c p < 10, else Hoermann's BTRS, with binary64 log and exp
+ * from their series (no library math), so the pairs are a function of the
+ * table, the weights, k, seed and stream_id.
+ *
+ *   d_weights  the words the table was built from (same dtype), device
+ *   d_items, d_counts  output, capacity entries each (device)
+ *   d_npairs   output (device u64): pairs produced; when it exceeds capacity
+ *              the pairs past capacity were not written
+ * Asynchronous on `stream`; allocates frontier buffers on first use. */
+wrs_status wrs_table2_sample_os(wrs_table2 *t, const void *d_weights, wrs_dtype dtype, uint64_t k, uint64_t seed,
+                                uint64_t stream_id, uint32_t *d_items, uint64_t *d_counts, uint64_t capacity,
+                                uint64_t *d_npairs, void *stream);
+
 /*
  * Build without allocating (no counterpart in the paper).
  *

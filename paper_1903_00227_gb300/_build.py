@@ -19,8 +19,12 @@ INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared"]
 
+# libwrs: no multiply-add contraction, so that the OS-ND binomial deviates
+# (binary64 arithmetic) follow the written steps exactly.
+EXTRA = {"libwrs.so": ["-fmad=false"]}
+
 TARGETS = {
-    "libwrs.so": (["wrs.cu"], ["wrs_device.cuh", "wrs_kernels.cuh", "wrs_batch.cuh", "wrs_twolevel.cuh"], [os.path.join(INCLUDE, "wrs.h")]),
+    "libwrs.so": (["wrs.cu"], ["wrs_device.cuh", "wrs_kernels.cuh", "wrs_batch.cuh", "wrs_twolevel.cuh", "wrs_osnd.cuh"], [os.path.join(INCLUDE, "wrs.h")]),
     "libwrs_workloads.so": (["workloads.cu"], [], []),
 }
 
@@ -50,7 +54,7 @@ def build(force: bool = False, verbose: bool = False) -> list[str]:
         if not force and not _stale(out, deps):
             continue
         tmp = out + f".tmp{os.getpid()}"
-        cmd = [_nvcc(), *ARCH, *NVCC_FLAGS, "-I", INCLUDE, "-o", tmp, *src_paths]
+        cmd = [_nvcc(), *ARCH, *NVCC_FLAGS, *EXTRA.get(name, []), "-I", INCLUDE, "-o", tmp, *src_paths]
         if verbose:
             print(" ".join(cmd), flush=True)
         procs.append((subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT), tmp, out, cmd))

@@ -566,3 +566,4 @@ extern "C" wrs_status wrs_build_noalloc(const void *d_weights, uint64_t n, wrs_d
 
 #include "wrs_batch.cuh"
 #include "wrs_twolevel.cuh"
+#include "wrs_osnd.cuh"

@@ -343,6 +343,8 @@ struct wrs_table2 {
     uint64_t meta_cap;     // entries
     uint4 *buckets;        // all levels, level 0 first
     int host_status;
+    void *os_front;        // OS-ND frontiers (one entry per group of every level) and counters
+    uint64_t os_cap;
 };
 
 namespace {
@@ -538,6 +540,7 @@ void wrs_table2_free(wrs_table2 *t)
     cudaDeviceSynchronize();
     if (t->buckets) cudaFree(t->buckets);
     if (t->ws) cudaFree(t->ws);
+    if (t->os_front) cudaFree(t->os_front);
     delete t;
 }
 

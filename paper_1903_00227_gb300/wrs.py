@@ -97,6 +97,7 @@ _sig = {
     "wrs_table2_layout": ([_TBL, _P, _P], _I),
     "wrs_table2_download": ([_TBL, _P, _U64, _P, _U64], _I),
     "wrs_table2_free": ([_TBL], None),
+    "wrs_table2_sample_os": ([_TBL, _P, _I, _U64, _U64, _U64, _P, _P, _U64, _P, _P], _I),
 }
 for _name, (_args, _res) in _sig.items():
     _f = getattr(_lib, _name)
@@ -529,6 +530,12 @@ def table2_free(t) -> None:
     _lib.wrs_table2_free(t)
 
 
+def table2_sample_os(t, d_weights: int, dtype: int, k: int, seed: int, stream_id: int, d_items: int,
+                     d_counts: int, capacity: int, d_npairs: int, stream: int = 0) -> int:
+    return _lib.wrs_table2_sample_os(t, d_weights, dtype, k, seed, stream_id, d_items, d_counts, capacity,
+                                     d_npairs, stream)
+
+
 class AliasTable2:
     """Owns one two-level ("2lvl-sweep") table (``wrs_table2``)."""
 
@@ -559,6 +566,26 @@ class AliasTable2:
 
     def status(self) -> int:
         return table2_status(self.handle)
+
+    def sample_os(self, weights, k: int, seed: int, stream_id: int = 0, capacity: int | None = None,
+                  stream=None):
+        """OS-ND sampling: (items, counts) CUDA tensors of the pairs drawn
+        (synchronises to read their number).  ``weights`` are the words the
+        table was built from."""
+        import torch
+
+        if capacity is None:
+            capacity = min(k, self.n + 128 * (self.n // TABLE2_GROUP + 1)) + 1
+        items = torch.empty(max(capacity, 1), dtype=torch.int32, device="cuda")
+        counts = torch.empty(max(capacity, 1), dtype=torch.int64, device="cuda")
+        npairs = torch.zeros(1, dtype=torch.int64, device="cuda")
+        _check(table2_sample_os(self.handle, weights.data_ptr(), _dtype_code(weights), k, seed, stream_id,
+                                items.data_ptr(), counts.data_ptr(), capacity, npairs.data_ptr(),
+                                _stream_handle(stream)), "wrs_table2_sample_os")
+        m = int(npairs.item())
+        if m > capacity:
+            raise WrsError(ENOMEM, f"wrs_table2_sample_os: {m} pairs exceed the capacity {capacity}")
+        return items[:m], counts[:m]
 
     def levels(self):
         rc, sizes = table2_layout(self.handle)
