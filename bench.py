@@ -307,6 +307,53 @@ def run_two_level(args, torch, wrs, weights, names, stream, peak):
                     "a different table from the headline's PSA table, same sampling distribution"}
 
 
+def run_os_nd(args, torch, wrs, weights, stream):
+    """OS-ND output-sensitive sampling (wrs_table2_sample_os) on the two-level
+    table of the skewed inputs, against k alias queries of the same table
+    (timed for k <= 10^9; the alias time of larger k is that rate)."""
+    n = args.n
+    sh = stream.cuda_stream
+    t2 = wrs.AliasTable2(n)
+    cap = n + 128 * (n // wrs.TABLE2_GROUP + 1) + 1
+    items = torch.empty(cap, dtype=torch.int32, device="cuda")
+    counts = torch.empty(cap, dtype=torch.int64, device="cuda")
+    npairs = torch.zeros(1, dtype=torch.int64, device="cuda")
+    qout = torch.empty(min(args.k, 10 ** 9), dtype=torch.int32, device="cuda")
+    res = {}
+    for name in [d for d in ("zipf1.5", "zipf0.8") if d in weights]:
+        w = weights[name]
+        t2.build(w, stream=sh)
+        ks = (10 ** 9, 10 ** 12) if name == "zipf1.5" else (10 ** 12,)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        kq = qout.numel()
+        t2.sample(kq, 3, out=qout, stream=sh)
+        e0.record(stream)
+        t2.sample(kq, 4, out=qout, stream=sh)
+        e1.record(stream)
+        e1.synchronize()
+        alias_rate = kq / (e0.elapsed_time(e1) * 1e-3)
+        for k in ks:
+            ts = []
+            for i in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                rc = wrs.table2_sample_os(t2.handle, w.data_ptr(), wrs.F32, k, 50 + i, 0, items.data_ptr(),
+                                          counts.data_ptr(), cap, npairs.data_ptr(), sh)
+                e1.record(stream)
+                e1.synchronize()
+                assert rc == wrs.OK, wrs.status_str(rc)
+                if i:
+                    ts.append(e0.elapsed_time(e1))
+            m = int(npairs.item())
+            assert m <= cap and int(counts[:m].sum().item()) == k
+            ms = statistics.mean(ts)
+            res[f"{name}_k{k:.0e}"] = {"k": k, "pairs": m, "ms": ms, "gsamples_s": k / (ms * 1e-3) / 1e9,
+                                       "alias_queries_ms_equivalent": k / alias_rate * 1e3,
+                                       "speedup_vs_alias": (k / alias_rate * 1e3) / ms}
+    t2.free()
+    return res
+
+
 def run_batched(args, torch, WL, wrs, stream):
     """Many-distribution workload: 4096 tables, sizes log-uniform in [32, 2^20],
     binary32 uniform or Zipf(1.0) by seed, k log-uniform in [1, 4096].  One
@@ -570,6 +617,7 @@ def run_ours(args, names):
     two_level = None
     if not args.no_two_level:
         two_level = run_two_level(args, torch, wrs, weights, names, stream, peak)
+        two_level["os_nd"] = run_os_nd(args, torch, wrs, weights, stream)
 
     batched = None
     if args.batch_tables > 0:
