@@ -3,7 +3,7 @@
 Tables must be identical bucket for bucket (thresholds and aliases) to the
 oracle's Alg. 2 table, the header (Q, beta, shift, qp, light count) must match
 the oracle's exact units, and samples must be identical index for index to
-the oracle's queries (integer work: bit-exact).  Sizes span several 4096-item
+the oracle's queries (integer work: bit-exact).  Sizes span several 2048-item
 tiles with ragged tails; inputs include the paper's workload shapes
 (uniform, Zipf-permuted) and degenerate ones.
 """
