@@ -85,10 +85,22 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def source_sha() -> str:
+KERNEL_SOURCES = {  # the files each measured kernel is compiled from
+    "psa": ("paper_1903_00227_gb300/csrc/wrs_kernels.cuh", "paper_1903_00227_gb300/csrc/wrs_device.cuh"),
+    "two_level": ("paper_1903_00227_gb300/csrc/wrs_kernels.cuh", "paper_1903_00227_gb300/csrc/wrs_device.cuh",
+                  "paper_1903_00227_gb300/csrc/wrs_twolevel.cuh"),
+    "os_nd": ("paper_1903_00227_gb300/csrc/wrs_kernels.cuh", "paper_1903_00227_gb300/csrc/wrs_device.cuh",
+              "paper_1903_00227_gb300/csrc/wrs_twolevel.cuh", "paper_1903_00227_gb300/csrc/wrs_osnd.cuh"),
+}
+
+
+def kernel_family(name: str) -> str:
+    return "os_nd" if name.startswith("k_os") else ("two_level" if name.startswith("k2_") else "psa")
+
+
+def source_sha(family: str = "psa") -> str:
     h = hashlib.sha256()
-    for rel in ("paper_1903_00227_gb300/csrc/wrs_kernels.cuh", "paper_1903_00227_gb300/csrc/wrs_device.cuh",
-                "paper_1903_00227_gb300/csrc/wrs_twolevel.cuh"):
+    for rel in KERNEL_SOURCES[family]:
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -96,17 +108,16 @@ def source_sha() -> str:
 
 def traffic_for(stage: str, units: int):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source; else None.  `stage` is a build stage or a
-    kernel name."""
+    on the current source of that kernel; else None.  `stage` is a build
+    stage or a kernel name."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         d = json.load(f)
-    if d.get("source_sha") != source_sha():
-        return None
-    e = d.get("kernels", {}).get(KERNEL_NAMES.get(stage, stage))
-    if not e:
+    name = KERNEL_NAMES.get(stage, stage)
+    e = d.get("kernels", {}).get(name)
+    if not e or e.get("source_sha") != source_sha(kernel_family(name)):
         return None
     return float(e["dram_bytes_per_unit"]) * units
 
@@ -557,6 +568,10 @@ def run_ours(args, names):
     roofline = {"bound": "hbm", "kernel": KERNEL_NAMES[dom], "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "traffic": traffic_for(dom, units[dom]),
                 "peak_source": peak_kind, "algorithmic_bytes_per_unit": ALGO_BYTES[dom]}
+    if roofline["traffic"]:  # DRAM bytes actually moved per launch (ncu) over the live duration
+        dram = roofline["traffic"] / (stage_ms[dom] * 1e-3) / 1e9
+        roofline["dram_achieved"] = dram
+        roofline["dram_frac"] = dram / peak
     build_mean = t_build / K
     ach_build = BUILD_BYTES_PER_WEIGHT * n / (build_mean * 1e-3) / 1e9
     per_kernel = {KERNEL_NAMES[s]: {"ms": stage_ms[s],

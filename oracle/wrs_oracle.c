@@ -687,6 +687,18 @@ static double det_log(double x)
     return (double)e * 0.6931471805599453 + 2.0 * s * acc;
 }
 
+/* log(1 - p) for 0 <= p <= 1/2 without forming 1 - p when p is small:    */
+/* -(p + p^2/2 + ... + p^40/40) for p < 1/4, else det_log(1 - p)           */
+static double det_log1m(double p)
+{
+    double acc;
+    int k;
+    if (p >= 0.25) return det_log(1.0 - p);
+    acc = 1.0 / 40.0;
+    for (k = 39; k >= 1; --k) acc = acc * p + 1.0 / (double)k;
+    return -p * acc;
+}
+
 /* e^x: x = k ln2 + r, |r| <= ln2 / 2 (+ rounding), Taylor to r^20 */
 static double det_exp(double x)
 {
@@ -761,7 +773,7 @@ static uint64_t os_binomial(uint64_t n, u128 num, u128 den, os_rng *rng)
     p = det_u128_to_double(num) / det_u128_to_double(den);
     q = 1.0 - p;
     if ((double)n * p < 10.0) { /* inversion */
-        const double s = p / q, a = ((double)n + 1.0) * s, r0 = det_exp((double)n * det_log(q));
+        const double s = p / q, a = ((double)n + 1.0) * s, r0 = det_exp((double)n * det_log1m(p));
         for (;;) {
             double u = os_unif(rng), r = r0;
             x = 0;
@@ -914,4 +926,5 @@ uint64_t wo_binomial(uint64_t n, uint64_t num, uint64_t den, uint64_t seed, uint
 }
 
 double wo_det_log(double x) { return det_log(x); }
+double wo_det_log1m(double p) { return det_log1m(p); }
 double wo_det_exp(double x) { return det_exp(x); }

@@ -93,6 +93,8 @@ def lib():
             L.wo_det_log.restype = ctypes.c_double
             L.wo_det_exp.argtypes = [ctypes.c_double]
             L.wo_det_exp.restype = ctypes.c_double
+            L.wo_det_log1m.argtypes = [ctypes.c_double]
+            L.wo_det_log1m.restype = ctypes.c_double
             _lib = L
     return _lib
 
@@ -112,7 +114,7 @@ class use_library:
         for name in ("wo_quantize", "wo_sweep", "wo_vose", "wo_psa", "wo_vose_f64", "wo_encode",
                      "wo_philox4x32_10", "wo_sample", "wo_sample_at", "wo_2lvl_levels", "wo_2lvl_build",
                      "wo_2lvl_sample", "wo_2lvl_sample_at", "wo_os_nd", "wo_binomial", "wo_det_log",
-                     "wo_det_exp"):
+                     "wo_det_exp", "wo_det_log1m"):
             f, g = getattr(L, name), getattr(self.saved, name)
             f.argtypes, f.restype = g.argtypes, g.restype
         with _lock:
@@ -360,3 +362,7 @@ def det_log(x: float) -> float:
 
 def det_exp(x: float) -> float:
     return float(lib().wo_det_exp(x))
+
+
+def det_log1m(p: float) -> float:
+    return float(lib().wo_det_log1m(p))

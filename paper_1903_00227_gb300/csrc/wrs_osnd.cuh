@@ -71,6 +71,16 @@ __device__ __forceinline__ double os_log(double x)
     return (double)e * 0.6931471805599453 + 2.0 * s * acc;
 }
 
+// log(1 - p) for 0 <= p <= 1/2 without forming 1 - p when p is small:
+// -(p + p^2/2 + ... + p^40/40) for p < 1/4, else os_log(1 - p)
+__device__ __forceinline__ double os_log1m(double p)
+{
+    if (p >= 0.25) return os_log(1.0 - p);
+    double acc = 1.0 / 40.0;
+    for (int k = 39; k >= 1; --k) acc = acc * p + 1.0 / (double)k;
+    return -p * acc;
+}
+
 // e^x: x = k ln2 + r, Taylor series of e^r to r^20
 __device__ __forceinline__ double os_exp(double x)
 {
@@ -136,7 +146,7 @@ __device__ uint64_t os_binomial(uint64_t n, u128 num, u128 den, OsRng &rng)
     const double p = os_u128_to_double(num) / os_u128_to_double(den), q = 1.0 - p;
     uint64_t x;
     if ((double)n * p < 10.0) { // inversion
-        const double s = p / q, a = ((double)n + 1.0) * s, r0 = os_exp((double)n * os_log(q));
+        const double s = p / q, a = ((double)n + 1.0) * s, r0 = os_exp((double)n * os_log1m(p));
         for (;;) {
             double u = os_unif(rng), r = r0;
             x = 0;

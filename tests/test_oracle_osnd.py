@@ -23,6 +23,25 @@ def test_series_log_exp():
     assert O.det_exp(-746.0) == 0.0
 
 
+def test_series_log1m():
+    for p in [1e-300, 1e-18, 1e-12, 3e-7, 1e-3, 0.1, 0.2499, 0.25, 0.3, 0.5]:
+        want = math.log1p(-p)
+        assert abs(O.det_log1m(p) - want) <= 4e-16 * abs(want), p
+
+
+def test_binomial_tiny_p_huge_n():
+    """n p = 3 with n = 10^12: P(X = 0) = e^-3 to 1e-12 relative; the
+    frequencies of 0 and of small values follow the Poisson limit."""
+    N = 20_000
+    draws = np.array([O.binomial(10 ** 12, 3, 10 ** 12, 5, node) for node in range(N)], dtype=np.int64)
+    pmf = scipy_stats.binom.pmf(np.arange(12), 10 ** 12, 3e-12)
+    obs = np.bincount(np.minimum(draws, 11), minlength=12)
+    e = pmf * N
+    e[11] = N - e[:11].sum()
+    chi = float(((obs - e) ** 2 / e).sum())
+    assert chi < 12 + 6 * math.sqrt(24), chi
+
+
 def _chi2(draws, n, p):
     pmf = scipy_stats.binom.pmf(np.arange(n + 1), n, p) if n <= 10 ** 6 else None
     if pmf is None:  # bin the support around the mean
