@@ -222,6 +222,20 @@ __global__ void k_os_init(OsFront *top, unsigned long long *ctr, uint32_t top_le
     }
 }
 
+// A group of the level below receiving c samples: level-0 groups that will
+// take the base case go to their own list (drawn by k_os_small0, a warp per
+// group); all others to the next frontier.
+__device__ __forceinline__ void os_push(uint32_t level, uint32_t member, uint64_t c, OsFront *next,
+                                        unsigned long long *nnext, OsFront *next_small,
+                                        unsigned long long *nnext_small, uint64_t N_next)
+{
+    OsFront f;
+    f.c = c; f.g = member; f.pad = 0;
+    const uint64_t ngn = min((uint64_t)kTile, N_next - (uint64_t)member * kTile);
+    if (level == 1 && c < kOsBase && 2 * ngn >= c) next_small[atomicAdd(nnext_small, 1ull)] = f;
+    else next[atomicAdd(nnext, 1ull)] = f;
+}
+
 // One frontier entry per block iteration.  SRC as k2_group.
 template <int SRC>
 __global__ void __launch_bounds__(kThreads) k_os_level(const void *__restrict__ src, int vec, uint64_t N,
@@ -230,6 +244,8 @@ __global__ void __launch_bounds__(kThreads) k_os_level(const void *__restrict__ 
                                                        const OsFront *__restrict__ front,
                                                        const unsigned long long *__restrict__ nfront,
                                                        OsFront *__restrict__ next, unsigned long long *nnext,
+                                                       OsFront *__restrict__ next_small,
+                                                       unsigned long long *nnext_small, uint64_t N_next,
                                                        uint32_t *__restrict__ items, uint64_t *__restrict__ counts,
                                                        unsigned long long *nout, uint64_t cap, uint64_t seed,
                                                        uint64_t stream)
@@ -270,12 +286,8 @@ __global__ void __launch_bounds__(kThreads) k_os_level(const void *__restrict__ 
                         if (s == np) { S.pick[np] = S.pick[t]; S.cnt[np] = 0; ++np; }
                         ++S.cnt[s];
                     }
-                    for (uint32_t s = 0; s < np; ++s) {
-                        const unsigned long long at = atomicAdd(nnext, 1ull);
-                        OsFront f;
-                        f.c = S.cnt[s]; f.g = S.pick[s]; f.pad = 0;
-                        next[at] = f;
-                    }
+                    for (uint32_t s = 0; s < np; ++s)
+                        os_push(level, S.pick[s], S.cnt[s], next, nnext, next_small, nnext_small, N_next);
                 }
                 __syncthreads();
             }
@@ -326,12 +338,7 @@ __global__ void __launch_bounds__(kThreads) k_os_level(const void *__restrict__ 
                 const OsNode d = S.node[cur][i];
                 if (d.b - d.a == 1) { // a leaf: an item, or a group one level down
                     if (level == 0) os_emit(items, counts, nout, cap, (uint32_t)(base + d.a), d.c);
-                    else {
-                        const unsigned long long at = atomicAdd(nnext, 1ull);
-                        OsFront f;
-                        f.c = d.c; f.g = (uint32_t)(base + d.a); f.pad = 0;
-                        next[at] = f;
-                    }
+                    else os_push(level, (uint32_t)(base + d.a), d.c, next, nnext, next_small, nnext_small, N_next);
                     continue;
                 }
                 const uint32_t mid = d.a + (d.b - d.a) / 2;
@@ -361,6 +368,50 @@ __global__ void __launch_bounds__(kThreads) k_os_level(const void *__restrict__ 
             __syncthreads();
         }
         __syncthreads();
+    }
+}
+
+// Level-0 groups with fewer than 128 samples (and at least half as many
+// members): a warp per group draws them as alias queries, one (item, 1) pair
+// each, with one output atomic per 32 queries.
+__global__ void __launch_bounds__(256) k_os_small0(uint64_t N, const uint4 *__restrict__ buckets,
+                                                   const GroupRec *__restrict__ groups, const DevHeader *hdr,
+                                                   const OsFront *__restrict__ front,
+                                                   const unsigned long long *__restrict__ nfront,
+                                                   uint32_t *__restrict__ items, uint64_t *__restrict__ counts,
+                                                   unsigned long long *nout, uint64_t cap, uint64_t seed,
+                                                   uint64_t stream)
+{
+    if (*(volatile const uint32_t *)&hdr->status) return;
+    const uint64_t nf = *nfront;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t e = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < nf; e += nwarps) {
+        const OsFront F = front[e];
+        const uint64_t base = (uint64_t)F.g * kTile;
+        const uint64_t ng = min((uint64_t)kTile, N - base);
+        const uint64_t qp = groups[F.g].qp;
+        for (uint32_t t0 = 0; t0 < (uint32_t)F.c; t0 += 32) {
+            const uint32_t t = t0 + lane;
+            const bool act = t < (uint32_t)F.c;
+            uint32_t pick = 0;
+            if (act) {
+                P4 ctr;
+                ctr.x0 = F.g; ctr.x1 = t << 14; // level 0, heap index 0
+                ctr.x2 = (uint32_t)stream; ctr.x3 = (uint32_t)(stream >> 32);
+                const P4 o = philox4x32_10(ctr, (uint32_t)seed, (uint32_t)(seed >> 32));
+                const uint64_t u = o.x0 | ((uint64_t)o.x1 << 32), v = o.x2 | ((uint64_t)o.x3 << 32);
+                const uint64_t r = __umul64hi(u, ng);
+                const uint4 bk = buckets[base + r];
+                const uint64_t thr = bk.x | ((uint64_t)bk.y << 32);
+                pick = (__umul64hi(v, qp) < thr) ? (uint32_t)(base + r) : bk.z;
+            }
+            const uint32_t m = __ballot_sync(0xFFFFFFFFu, act);
+            unsigned long long at = 0;
+            if (lane == 0) at = atomicAdd(nout, (unsigned long long)__popc(m));
+            at = __shfl_sync(0xFFFFFFFFu, at, 0) + lane; // the active lanes are a prefix
+            if (act && at < cap) { items[at] = pick; counts[at] = 1; }
+        }
     }
 }
 
@@ -403,14 +454,16 @@ wrs_status wrs_table2_sample_os(wrs_table2 *t, const void *d_weights, wrs_dtype 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const Levels &v = t->lv;
     const uint64_t ngroups = levels_groups(v);
-    if (t->os_cap < ngroups + 2) { // frontier buffers: one entry per group of every level, and counters
+    const uint64_t need = ngroups + (v.size[0] + kTile - 1) / kTile + 2; // + the level-0 small list
+    if (t->os_cap < need) { // frontier buffers: one entry per group of every level, and counters
         if (t->os_front) { cudaDeviceSynchronize(); cudaFree(t->os_front); t->os_front = nullptr; t->os_cap = 0; }
-        cudaError_t e = cudaMalloc(&t->os_front, (ngroups + 2) * sizeof(OsFront) + 8 * sizeof(unsigned long long));
+        cudaError_t e = cudaMalloc(&t->os_front, need * sizeof(OsFront) + 8 * sizeof(unsigned long long));
         if (e != cudaSuccess) return cuda_err(e);
-        t->os_cap = ngroups + 2;
+        t->os_cap = need;
     }
     OsFront *fr = static_cast<OsFront *>(t->os_front);
-    unsigned long long *ctr = reinterpret_cast<unsigned long long *>(fr + t->os_cap); // [level] frontier sizes
+    OsFront *small0 = fr + ngroups; // level-0 groups for the base case
+    unsigned long long *ctr = reinterpret_cast<unsigned long long *>(fr + t->os_cap); // [level] frontier sizes, [4] small0
     k_os_init<<<1, 32, 0, s>>>(fr + v.goff[v.L - 1], ctr, v.L - 1, reinterpret_cast<unsigned long long *>(d_npairs),
                                k);
     if (k == 0) return launch_err();
@@ -422,15 +475,19 @@ wrs_status wrs_table2_sample_os(wrs_table2 *t, const void *d_weights, wrs_dtype 
         const OsFront *cur = fr + v.goff[l];
         OsFront *nxt = l > 0 ? fr + v.goff[l - 1] : nullptr;
         unsigned long long *nnext = l > 0 ? ctr + (l - 1) : ctr + 7;
+        const uint64_t N_next = l > 0 ? v.size[l - 1] : 0;
         const uint4 *bk = t->buckets + v.off[l];
         const GroupRec *gr = t->groups + v.goff[l];
         unsigned long long *nout = reinterpret_cast<unsigned long long *>(d_npairs);
         if (l == 0) {
-            if (t->f32) k_os_level<1><<<blocks, kThreads, smem, s>>>(d_weights, (reinterpret_cast<uintptr_t>(d_weights) % 16) == 0, v.size[0], 0, bk, gr, t->hdr, cur, ctr + 0, nxt, nnext, d_items, d_counts, nout, capacity, seed, stream_id);
-            else k_os_level<0><<<blocks, kThreads, smem, s>>>(d_weights, (reinterpret_cast<uintptr_t>(d_weights) % 16) == 0, v.size[0], 0, bk, gr, t->hdr, cur, ctr + 0, nxt, nnext, d_items, d_counts, nout, capacity, seed, stream_id);
+            const int vec = (reinterpret_cast<uintptr_t>(d_weights) % 16) == 0;
+            k_os_small0<<<(uint32_t)sm_count() * 8, 256, 0, s>>>(v.size[0], bk, gr, t->hdr, small0, ctr + 4, d_items,
+                                                                 d_counts, nout, capacity, seed, stream_id);
+            if (t->f32) k_os_level<1><<<blocks, kThreads, smem, s>>>(d_weights, vec, v.size[0], 0, bk, gr, t->hdr, cur, ctr + 0, nxt, nnext, small0, ctr + 4, N_next, d_items, d_counts, nout, capacity, seed, stream_id);
+            else k_os_level<0><<<blocks, kThreads, smem, s>>>(d_weights, vec, v.size[0], 0, bk, gr, t->hdr, cur, ctr + 0, nxt, nnext, small0, ctr + 4, N_next, d_items, d_counts, nout, capacity, seed, stream_id);
         } else {
             const uint64_t *meta_in = t->meta + 2 * (v.off[l] - t->n);
-            k_os_level<2><<<blocks, kThreads, smem, s>>>(meta_in, 1, v.size[l], (uint32_t)l, bk, gr, t->hdr, cur, ctr + l, nxt, nnext, d_items, d_counts, nout, capacity, seed, stream_id);
+            k_os_level<2><<<blocks, kThreads, smem, s>>>(meta_in, 1, v.size[l], (uint32_t)l, bk, gr, t->hdr, cur, ctr + l, nxt, nnext, small0, ctr + 4, N_next, d_items, d_counts, nout, capacity, seed, stream_id);
         }
     }
     return launch_err();
