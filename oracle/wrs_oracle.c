@@ -928,3 +928,115 @@ uint64_t wo_binomial(uint64_t n, uint64_t num, uint64_t den, uint64_t seed, uint
 double wo_det_log(double x) { return det_log(x); }
 double wo_det_log1m(double p) { return det_log1m(p); }
 double wo_det_exp(double x) { return det_exp(x); }
+
+/* ------------------------------------------------------------------------ */
+/* PSA+ (Sec. 4.2 "Performance Optimization in Practice"): each tile of T    */
+/* consecutive items (the PE's allotment) first runs Alg. 2 on its own items */
+/* in the global units (capacity Q, item i weighs n q_i), stopping when the  */
+/* next light or the next heavy item would lie outside the tile; the items   */
+/* left over -- the heavy item current at the stop with its unassigned       */
+/* residual, every other unassigned item with its full weight -- form, in    */
+/* index order, a list on which Alg. 2 (equivalently PSA) builds the rest.   */
+/* Reading: a heavy item is packed once its residual is <= Q, which needs    */
+/* the next heavy item of the tile as its alias; a light item needs a        */
+/* current heavy item.                                                        */
+/* ------------------------------------------------------------------------ */
+
+/* Alg. 2 on m items of scaled weights v (two words each; the capacity is  */
+/* Q and sum v = m Q), writing bucket masses and aliases at idx[] of the     */
+/* full table.                                                                */
+static int sweep_scaled(uint64_t m, const uint64_t *v, const uint32_t *idx, u128 Q, uint64_t *bw, uint32_t *al)
+{
+    uint64_t i = 0, j = 0, k;
+    u128 w;
+#define V(t) ld128(v + 2 * (t))
+    while (i < m && V(i) > Q) ++i;           /* first light */
+    while (j < m && V(j) <= Q) ++j;          /* first heavy */
+    if (j == m) {                            /* all full */
+        for (k = 0; k < m; ++k) {
+            if (V(k) != Q) return WO_EINTERNAL;
+            put(bw, al, idx[k], Q, idx[k]);
+        }
+        return WO_OK;
+    }
+    w = V(j);
+    while (j < m) {
+        if (w > Q) {
+            if (i >= m) return WO_EINTERNAL;
+            put(bw, al, idx[i], V(i), idx[j]);
+            w = (w + V(i)) - Q;
+            do { ++i; } while (i < m && V(i) > Q);
+        } else {
+            uint64_t jn = j + 1;
+            while (jn < m && V(jn) <= Q) ++jn;
+            put(bw, al, idx[j], w, jn < m ? idx[jn] : idx[j]);
+            if (jn < m) w = (w + V(jn)) - Q;
+            else if (w != Q) return WO_EINTERNAL;
+            j = jn;
+        }
+    }
+    for (; i < m; ) {
+        if (V(i) != Q) return WO_EINTERNAL;
+        put(bw, al, idx[i], Q, idx[i]);
+        do { ++i; } while (i < m && V(i) > Q);
+    }
+#undef V
+    return WO_OK;
+}
+
+int wo_psa_plus(uint64_t n, const uint64_t *q, const uint64_t *Qin, uint64_t T, uint64_t *bw, uint32_t *al,
+                uint64_t *n_left)
+{
+    wo_in in = { n, q, ld128(Qin) };
+    const u128 Q = in.Q;
+    uint64_t *lv = (uint64_t *)malloc(2 * (n + 1) * sizeof(uint64_t));
+    uint32_t *lidx = (uint32_t *)malloc((n + 1) * sizeof(uint32_t));
+    uint64_t m = 0, t0, b;
+    int rc;
+    if (!lv || !lidx || T == 0) { free(lv); free(lidx); return WO_EINVAL; }
+    for (t0 = 0; t0 < n; t0 += T) {
+        const uint64_t t1 = (n - t0 < T) ? n : t0 + T;
+        uint64_t i = t0, j = t0, k, cur = t1; /* cur: the heavy item current at the stop */
+        u128 w = 0;
+        unsigned char *done = (unsigned char *)calloc(t1 - t0, 1);
+        if (!done) { free(lv); free(lidx); return WO_EINVAL; }
+        while (i < t1 && !is_light(&in, i)) ++i;
+        while (j < t1 && is_light(&in, j)) ++j;
+        if (j < t1) {
+            w = nq(&in, j);
+            for (;;) {
+                if (w > Q) { /* needs a light */
+                    if (i >= t1) break;
+                    put(bw, al, i, nq(&in, i), j);
+                    done[i - t0] = 1;
+                    w = (w + nq(&in, i)) - Q;
+                    do { ++i; } while (i < t1 && !is_light(&in, i));
+                } else { /* pack heavy j: needs the next heavy */
+                    uint64_t jn = j + 1;
+                    while (jn < t1 && is_light(&in, jn)) ++jn;
+                    if (jn >= t1) break;
+                    put(bw, al, j, w, jn);
+                    done[j - t0] = 1;
+                    w = (w + nq(&in, jn)) - Q;
+                    j = jn;
+                }
+            }
+            cur = j;
+        }
+        for (k = t0; k < t1; ++k) {
+            if (done[k - t0]) continue;
+            st128(lv + 2 * m, k == cur ? w : nq(&in, k));
+            lidx[m] = (uint32_t)k;
+            ++m;
+        }
+        free(done);
+    }
+    rc = sweep_scaled(m, lv, lidx, Q, bw, al);
+    free(lv);
+    free(lidx);
+    if (rc) return rc;
+    for (b = 0; b < n; ++b)
+        if (ld128(bw + 2 * b) == Q) al[b] = (uint32_t)b;
+    if (n_left) *n_left = m;
+    return WO_OK;
+}

@@ -95,6 +95,8 @@ def lib():
             L.wo_det_exp.restype = ctypes.c_double
             L.wo_det_log1m.argtypes = [ctypes.c_double]
             L.wo_det_log1m.restype = ctypes.c_double
+            L.wo_psa_plus.argtypes = [U64, P, P, U64, P, P, P]
+            L.wo_psa_plus.restype = INT
             _lib = L
     return _lib
 
@@ -114,7 +116,7 @@ class use_library:
         for name in ("wo_quantize", "wo_sweep", "wo_vose", "wo_psa", "wo_vose_f64", "wo_encode",
                      "wo_philox4x32_10", "wo_sample", "wo_sample_at", "wo_2lvl_levels", "wo_2lvl_build",
                      "wo_2lvl_sample", "wo_2lvl_sample_at", "wo_os_nd", "wo_binomial", "wo_det_log",
-                     "wo_det_exp", "wo_det_log1m"):
+                     "wo_det_exp", "wo_det_log1m", "wo_psa_plus"):
             f, g = getattr(L, name), getattr(self.saved, name)
             f.argtypes, f.restype = g.argtypes, g.restype
         with _lock:
@@ -209,6 +211,20 @@ def _construct(fn, qz: Quantized, *extra) -> Table:
     if rc:
         raise OracleError(rc, fn.__name__)
     return Table(bw, al, qz.Qw)
+
+
+def psa_plus(qz: Quantized, T: int = 2048, return_left: bool = False):
+    """PSA+ (Sec. 4.2 "Performance Optimization in Practice") with tiles of T
+    items; optionally also the number of items left to the second phase."""
+    n = qz.n
+    bw = np.zeros((n, 2), dtype=np.uint64)
+    al = np.zeros(n, dtype=np.uint32)
+    left = ctypes.c_uint64(0)
+    rc = lib().wo_psa_plus(n, _ptr(qz.q), _ptr(qz.Qw), T, _ptr(bw), _ptr(al), ctypes.addressof(left))
+    if rc:
+        raise OracleError(rc, "psa_plus")
+    t = Table(bw, al, qz.Qw)
+    return (t, left.value) if return_left else t
 
 
 def sweep(qz: Quantized) -> Table:
