@@ -67,6 +67,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-two-level", action="store_true")
+    ap.add_argument("--no-psa-plus", action="store_true")
     ap.add_argument("--batch-tables", type=int, default=4096,
                     help="tables of the many-distribution workload (0: skip it)")
     ap.add_argument("--batch-steps", type=int, default=10)
@@ -91,10 +92,14 @@ KERNEL_SOURCES = {  # the files each measured kernel is compiled from
                   "paper_1903_00227_gb300/csrc/wrs_twolevel.cuh"),
     "os_nd": ("paper_1903_00227_gb300/csrc/wrs_kernels.cuh", "paper_1903_00227_gb300/csrc/wrs_device.cuh",
               "paper_1903_00227_gb300/csrc/wrs_twolevel.cuh", "paper_1903_00227_gb300/csrc/wrs_osnd.cuh"),
+    "psa_plus": ("paper_1903_00227_gb300/csrc/wrs_kernels.cuh", "paper_1903_00227_gb300/csrc/wrs_device.cuh",
+                 "paper_1903_00227_gb300/csrc/wrs_twolevel.cuh", "paper_1903_00227_gb300/csrc/wrs_psaplus.cuh"),
 }
 
 
 def kernel_family(name: str) -> str:
+    if name.startswith("k_pp"):
+        return "psa_plus"
     return "os_nd" if name.startswith("k_os") else ("two_level" if name.startswith("k2_") else "psa")
 
 
@@ -318,6 +323,46 @@ def run_two_level(args, torch, wrs, weights, names, stream, peak):
             "levels": levels, "per_dist": per,
             "note": "wrs_table2_*: Alg. 2 per group of 2048, group totals as the next level (Sec. 6); "
                     "a different table from the headline's PSA table, same sampling distribution"}
+
+
+PSA_PLUS_BYTES_PER_WEIGHT = 20  # two 4-B weight reads + 12-B payload (the leftovers' passes come on top)
+
+
+def run_psa_plus(args, torch, wrs, table, weights, names, stream, peak):
+    """PSA+ builds (wrs_table_build_psa_plus) of the same inputs into the
+    headline's table object, CUDA events on the launching stream; the sampler
+    is the headline's (same table format)."""
+    n = args.n
+    sh = stream.cuda_stream
+    per = {}
+    for name in names:
+        w = weights[name]
+        for _ in range(2):
+            table.build_psa_plus(w, stream=sh)
+        torch.cuda.synchronize()
+        bt = []
+        for i in range(max(3, args.steps // 2)):
+            e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+            e0.record(stream)
+            table.build_psa_plus(w, stream=sh)
+            e1.record(stream)
+            e1.synchronize()
+            bt.append(e0.elapsed_time(e1))
+        if table.status() != wrs.OK:
+            raise RuntimeError("PSA+ build failed")
+        left = table.psa_plus_leftovers()
+        bm = statistics.mean(bt)
+        per[name] = {"build_ms": bm, "build_gweights_s": n / (bm * 1e-3) / 1e9,
+                     "build_frac": PSA_PLUS_BYTES_PER_WEIGHT * n / (bm * 1e-3) / 1e9 / peak,
+                     "leftover_fraction": left / n}
+    bmean = statistics.mean(v["build_ms"] for v in per.values())
+    ach = PSA_PLUS_BYTES_PER_WEIGHT * n / (bmean * 1e-3) / 1e9
+    return {"build_gweights_s": n / (bmean * 1e-3) / 1e9,
+            "roofline_build": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                               "algorithmic_bytes_per_weight": PSA_PLUS_BYTES_PER_WEIGHT},
+            "per_dist": per,
+            "note": "wrs_table_build_psa_plus: Alg. 2 per tile of 2048 until an item outside the tile is needed, "
+                    "then PSA on the leftovers (Sec. 4.2); a different table from PSA's, same distribution"}
 
 
 def run_os_nd(args, torch, wrs, weights, stream):
@@ -631,6 +676,10 @@ def run_ours(args, names):
                "d2h_bytes_per_step": 4 * k, "ms_per_step": t_e2e,
                "note": "wrs_table_build_host (H2D of the weights) + wrs_sample_host (D2H of the samples)"}
 
+    psa_plus = None
+    if not args.no_psa_plus:
+        psa_plus = run_psa_plus(args, torch, wrs, table, weights, names, stream, peak)
+
     two_level = None
     if not args.no_two_level:
         two_level = run_two_level(args, torch, wrs, weights, names, stream, peak)
@@ -662,7 +711,7 @@ def run_ours(args, names):
                                "frac": ach_build / peak, "algorithmic_bytes_per_weight": BUILD_BYTES_PER_WEIGHT,
                                "peak_source": peak_kind},
             "kernels": per_kernel, "per_dist": per_dist,
-            "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "two_level": two_level, "many_tables": batched, "serving": serving,
+            "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "psa_plus": psa_plus, "two_level": two_level, "many_tables": batched, "serving": serving,
             "gpu_launches": K * (len(wrs.STAGES) + 1),
             "context": {"paper_psa_build_gweights_s_n1e9": 0.99, "paper_psa_query_gsamples_s_n1e9": 1.662,
                         "paper_hardware": "4x Xeon Gold 6138, 158 threads (context only)"},

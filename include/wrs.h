@@ -101,6 +101,28 @@ wrs_status wrs_table_create(uint64_t capacity_n, wrs_table **out);
 wrs_status wrs_table_build(wrs_table *t, const void *d_weights, uint64_t n,
                            wrs_dtype dtype, void *stream);
 
+/* Build the alias table of n weights with PSA+ (Sec. 4.2 "Performance
+ * Optimization in Practice"): every tile of 2048 consecutive items first runs
+ * Alg. 2 on its own items, in the global units (capacity Q, item i weighs
+ * n * q_i), until the next light or the next heavy item it needs lies outside
+ * the tile; the heavy item current at that point keeps its unassigned
+ * residual, and the items left over from all tiles, in index order, are built
+ * by Alg. 2 (PSA) as one list.  Full buckets point to themselves.  The table
+ * differs from wrs_table_build's (the tiles pair items locally) but obeys the
+ * same contract, and wrs_sample and every other table call accept it.
+ * Arguments, ownership and errors as for wrs_table_build.  The first PSA+
+ * build of a table allocates 40 B per weight of its capacity (synchronous
+ * cudaMalloc), kept until wrs_table_free; later builds allocate nothing and
+ * are asynchronous. */
+wrs_status wrs_table_build_psa_plus(wrs_table *t, const void *d_weights, uint64_t n,
+                                    wrs_dtype dtype, void *stream);
+
+/* Number of items the last build's tile phase left over (the length of the
+ * list the second phase built), when that build was wrs_table_build_psa_plus.
+ * Synchronises the device.  Errors: WRS_EINVAL (no PSA+ build is the table's
+ * last), WRS_EDEVICE. */
+wrs_status wrs_table_psa_plus_leftovers(const wrs_table *t, uint64_t *n_left);
+
 /* wrs_table_create(n) followed by wrs_table_build(). */
 wrs_status wrs_build(const void *d_weights, uint64_t n, wrs_dtype dtype,
                      void *stream, wrs_table **out);

@@ -40,6 +40,8 @@ struct wrs_table {
     cudaEvent_t ev[kStages + 1]; // stage timing (created when enabled)
     int timing;            // record ev[] around the build's kernels
     int timed_build;       // the last build recorded ev[]
+    uint8_t *pp_ws;        // PSA+ scratch (allocated by the first PSA+ build)
+    uint64_t pp_n;         // n of the last PSA+ build (0: the last build was not PSA+)
 };
 
 namespace {
@@ -155,6 +157,7 @@ wrs_status enqueue_build(wrs_table *t, const void *d_weights, uint64_t n, wrs_dt
     if (st == WRS_OK) {
         t->n = n;
         t->host_status = -1;
+        t->pp_n = 0;
     }
     return st;
 }
@@ -374,6 +377,7 @@ wrs_status wrs_table_upload(wrs_table *t, const void *h_buckets, uint64_t n, uin
     if (e != cudaSuccess) return cuda_err(e);
     t->n = n;
     t->host_status = 0;
+    t->pp_n = 0;
     return WRS_OK;
 }
 
@@ -419,6 +423,7 @@ void wrs_table_free(wrs_table *t)
     if (t->stage_out) cudaFree(t->stage_out);
     if (t->copy_stream) cudaStreamDestroy(t->copy_stream);
     if (t->copy_ev) cudaEventDestroy(t->copy_ev);
+    if (t->pp_ws) cudaFree(t->pp_ws);
     delete t;
 }
 
@@ -567,3 +572,4 @@ extern "C" wrs_status wrs_build_noalloc(const void *d_weights, uint64_t n, wrs_d
 #include "wrs_batch.cuh"
 #include "wrs_twolevel.cuh"
 #include "wrs_osnd.cuh"
+#include "wrs_psaplus.cuh"

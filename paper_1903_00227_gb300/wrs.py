@@ -57,6 +57,8 @@ _PTBL = ctypes.POINTER(ctypes.c_void_p)
 _sig = {
     "wrs_table_create": ([_U64, _PTBL], _I),
     "wrs_table_build": ([_TBL, _P, _U64, _I, _P], _I),
+    "wrs_table_build_psa_plus": ([_TBL, _P, _U64, _I, _P], _I),
+    "wrs_table_psa_plus_leftovers": ([_TBL, ctypes.POINTER(ctypes.c_uint64)], _I),
     "wrs_build": ([_P, _U64, _I, _P, _PTBL], _I),
     "wrs_sample": ([_TBL, _U64, _U64, _U64, _P, _P], _I),
     "wrs_table_build_host": ([_TBL, _P, _U64, _I, _P], _I),
@@ -131,6 +133,16 @@ def table_create(capacity_n: int):
 
 def table_build(t, d_weights: int, n: int, dtype: int, stream: int = 0) -> int:
     return _lib.wrs_table_build(t, d_weights, n, dtype, stream)
+
+
+def table_build_psa_plus(t, d_weights: int, n: int, dtype: int, stream: int = 0) -> int:
+    return _lib.wrs_table_build_psa_plus(t, d_weights, n, dtype, stream)
+
+
+def table_psa_plus_leftovers(t):
+    m = ctypes.c_uint64()
+    rc = _lib.wrs_table_psa_plus_leftovers(t, ctypes.byref(m))
+    return rc, m.value
 
 
 def build(d_weights: int, n: int, dtype: int, stream: int = 0):
@@ -337,6 +349,20 @@ class AliasTable:
                "wrs_table_build")
         self.n = n
         return self
+
+    def build_psa_plus(self, weights, stream=None) -> "AliasTable":
+        """PSA+ build (per-tile greedy pass, then PSA on the leftovers)."""
+        assert weights.is_cuda and weights.is_contiguous()
+        n = weights.numel()
+        _check(table_build_psa_plus(self.handle, weights.data_ptr(), n, _dtype_code(weights),
+                                    _stream_handle(stream)), "wrs_table_build_psa_plus")
+        self.n = n
+        return self
+
+    def psa_plus_leftovers(self) -> int:
+        rc, m = table_psa_plus_leftovers(self.handle)
+        _check(rc, "wrs_table_psa_plus_leftovers")
+        return m
 
     def sample(self, k: int, seed: int, stream_id: int = 0, out=None, stream=None):
         import torch

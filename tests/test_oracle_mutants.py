@@ -18,7 +18,9 @@ MUTANTS = {
     # Alg. 2: residual update drops the light item's weight
     "sweep_drop_term": ("            w = (w + nq(&in, i)) - in.Q;\n            i = next_light", "            w = w - in.Q + 1;\n            i = next_light"),
     # Alg. 2: light bucket takes the next heavy as alias instead of the current one
-    "sweep_alias_index": ("            put(bw, al, i, nq(&in, i), j);", "            put(bw, al, i, nq(&in, i), next_heavy(&in, j + 1) < n ? next_heavy(&in, j + 1) : j);"),
+    "sweep_alias_index": ("            put(bw, al, i, nq(&in, i), j);\n            w = (w + nq(&in, i)) - in.Q;",
+                          "            put(bw, al, i, nq(&in, i), next_heavy(&in, j + 1) < n ? next_heavy(&in, j + 1) : j);\n"
+                          "            w = (w + nq(&in, i)) - in.Q;"),
     # classification: light iff n*q < Q (strict)
     "light_strict": ("static int is_light(const wo_in *in, uint64_t k) { return nq(in, k) <= in->Q; }",
                      "static int is_light(const wo_in *in, uint64_t k) { return nq(in, k) < in->Q; }"),
