@@ -9,18 +9,20 @@
 // every other unassigned item whole -- form, in index order, the input of
 // Alg. 2 (= PSA) for the rest of the table.
 //
-// Phase 1 (k_pp_local, one block per tile): the tile's light keys D (prefix
-// of deficits Q - n q) and heavy keys E (prefix of excesses n q - Q), local
-// to the tile; with D_tot the tile's total deficit and E_last the last heavy
-// key, either the lights run out first (E_last > D_tot: every light is
-// packed, the heavies with E <= D_tot are packed, the next one stops with
-// residual) or the last heavy is covered first (the lights with D < E_last
-// are packed, every heavy but the last, which stops).  The packed items are
-// one merge, as in the single table's sweep; the leftovers are staged per
-// tile.  Phase 2: the leftovers are compacted (look-back scan of the tile
-// counts), their global keys are written once (lights and heavies apart,
-// look-back scan of per-tile sums), and one block per 2048 merge steps finds
-// its start by a warp-cooperative co-rank search over those keys and walks.
+// k_pp_local (one block per tile): the tile's light keys D (prefix of
+// deficits Q - n q) and heavy keys E (prefix of excesses n q - Q), local to
+// the tile; with D_tot the tile's total deficit and E_last its last heavy key,
+// either the lights run out first (E_last > D_tot: every light is packed, the
+// heavies with E <= D_tot are packed, the next one stops with its residual)
+// or the last heavy is covered first (the lights with D < E_last are packed,
+// every heavy but the last, which stops).  The packed items are one merge, as
+// in the single table's sweep.  The leftovers get keys local to the tile
+// (light iff v <= Q; deficits Q - v, excesses v - Q) in the tile's staging
+// slots, and the tile's sums and counts.  k_pp_scan1/k_pp_scan2 scan those
+// over the tiles, k_pp_keys adds the prefixes and moves every key to its
+// global rank (lights, then heavies), k_pp_starts finds where each block of
+// merge steps begins (co-rank search, one warp per block), and k_pp_merge
+// walks them.
 #pragma once
 
 namespace wrs {
@@ -35,12 +37,42 @@ __device__ __forceinline__ bool block_stopped(const DevHeader *hdr)
     return s_st != 0;
 }
 
+// Leftover sums of tiles: l = deficits of the lights (v <= Q), h = excesses
+// of the heavies, cl / nheavy = their counts (TileSum's fields).
+__device__ __forceinline__ void pp_add(TileSum &a, const TileSum &b)
+{
+    const u128 l = mk128(a.l_lo, a.l_hi) + mk128(b.l_lo, b.l_hi);
+    const u128 h = mk128(a.h_lo, a.h_hi) + mk128(b.h_lo, b.h_hi);
+    a.l_lo = lo64(l); a.l_hi = hi64(l); a.h_lo = lo64(h); a.h_hi = hi64(h);
+    a.cl += b.cl;
+    a.nheavy += b.nheavy;
+}
+
+__device__ __forceinline__ TileSum pp_zero()
+{
+    TileSum z;
+    z.l_lo = z.l_hi = z.h_lo = z.h_hi = 0;
+    z.cl = 0; z.nheavy = 0; z.first_heavy = kNone; z.pad = 0;
+    return z;
+}
+
+__device__ __forceinline__ void st_key(uint4 *p, u128 k)
+{
+    *p = make_uint4((uint32_t)lo64(k), (uint32_t)(lo64(k) >> 32), (uint32_t)hi64(k), (uint32_t)(hi64(k) >> 32));
+}
+
+__device__ __forceinline__ u128 ld_key(const uint4 *p)
+{
+    const uint4 r = __ldcg(p);
+    return mk128(r.x | ((uint64_t)r.y << 32), r.z | ((uint64_t)r.w << 32));
+}
+
 // ------------------------------------------------------------ phase 1
 template <int F32>
 __global__ void __launch_bounds__(kThreads, 3) k_pp_local(const uint32_t *__restrict__ w, uint64_t n, int vec,
                                                           DevHeader *hdr, uint4 *__restrict__ table,
-                                                          uint64_t *__restrict__ lo_v, uint32_t *__restrict__ lo_idx,
-                                                          TileSum *__restrict__ cnt_agg)
+                                                          TileSum *__restrict__ tsum, uint4 *__restrict__ skeys,
+                                                          uint32_t *__restrict__ sidx)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     GroupSmem &S = *reinterpret_cast<GroupSmem *>(smem_raw);
@@ -51,7 +83,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_pp_local(const uint32_t *__rest
     const u128 Q = mk128(hdr->q_lo, hdr->q_hi);
     const uint32_t light_max = hdr->light_max, shift = hdr->shift;
     const int beta = hdr->beta;
-    const uint64_t tile0 = (uint64_t)blockIdx.x * kTile;
+    const uint32_t tile = blockIdx.x;
+    const uint64_t tile0 = (uint64_t)tile * kTile;
     const uint64_t first = tile0 + (uint64_t)threadIdx.x * kItems;
     uint32_t x[kItems];
     load_items(w, n, vec, first, x);
@@ -126,292 +159,314 @@ __global__ void __launch_bounds__(kThreads, 3) k_pp_local(const uint32_t *__rest
     __syncthreads();
     const uint32_t A = s_ab[0], B = s_ab[1];
     bool bad = false;
-    // the packed items: lights [0, A) and heavies [0, B), one merge
+    // The leftovers: lights of rank >= A, heavies of rank > B, and heavy B
+    // (when there is one) with its residual; in the second phase an item is
+    // light iff its value v <= Q.  Their sums and their keys local to the
+    // tile follow from the tile's own keys: the leftover lights' deficits are
+    // D - D_A, the leftover heavies' excesses E - E_B, and heavy B adds
+    // Q - res to the lights after it or res - Q before the heavies.
+    const bool hasB = B < nh;
+    const u128 res = hasB ? s_res : (u128)0;
+    const bool Bl = hasB && res <= Q, Bh = hasB && res > Q;
+    const uint32_t offB = hasB ? S.hoff[B] : 0xFFFFFFFFu;
+    const u128 DA = A < nl ? S.okey[swz(A)] : D_tot;
+    const u128 EB = hasB ? S.hkey[swz(B)] : (u128)0;
+    const uint32_t ncl = (nl - A) + (Bl ? 1u : 0u);
+    const uint32_t nch = hasB ? (nh - B - 1) + (Bh ? 1u : 0u) : 0u;
+    if (threadIdx.x == 0) {
+        const u128 lsum = (D_tot - DA) + (Bl ? Q - res : (u128)0);
+        const u128 hsum = hasB ? (S.hkey[swz(nh - 1)] - EB) + (Bh ? res - Q : (u128)0) : (u128)0;
+        TileSum a;
+        a.l_lo = lo64(lsum); a.l_hi = hi64(lsum); a.h_lo = lo64(hsum); a.h_hi = hi64(hsum);
+        a.cl = ncl; a.nheavy = nch; a.first_heavy = kNone; a.pad = 0;
+        tilesum_st(tsum + tile, a);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&hdr->n_light), (unsigned long long)nl);
+    }
+    // the packed items, lights [0, A) and heavies [0, B), as one merge
     const uint32_t M = A + B;
-    if (M > 0) {
-        const uint32_t per = (M + kThreads - 1) / kThreads;
-        const uint32_t d0 = threadIdx.x * per;
-        if (d0 < M) {
-            uint32_t lo = d0 > A ? d0 - A : 0, hi = d0 < B ? d0 : B;
-            while (lo < hi) {
-                const uint32_t mid = (lo + hi + 1) >> 1;
-                if (S.hkey[swz(mid - 1)] <= S.okey[swz(d0 - mid)]) lo = mid; else hi = mid - 1;
-            }
-            uint32_t j = lo, i = d0 - lo;
-            const uint32_t steps = min(per, M - d0);
-            u128 ej = j < nh ? S.hkey[swz(j)] : (u128)0;
-            u128 di = i < nl ? S.okey[swz(i)] : D_tot;
-            for (uint32_t st = 0; st < steps; ++st) {
-                if ((j < B) && (i >= A || ej <= di)) { // heavy j: Q - (D_i - E_j), alias the next heavy (in the tile)
-                    const u128 gap = di - ej;
-                    if (gap > Q || j + 1 >= nh) bad = true;
-                    const uint32_t me = (uint32_t)(tile0 + S.hoff[j]);
-                    const uint32_t nx = (uint32_t)(tile0 + S.hoff[min(j + 1, nh - 1)]);
-                    const uint32_t alias = gap == 0 ? me : nx;
-                    const uint64_t thr = lo64((Q - gap) >> shift);
-                    table[me] = make_uint4((uint32_t)thr, (uint32_t)(thr >> 32), alias, 0u);
-                    ++j;
-                    if (j < nh) ej = S.hkey[swz(j)];
-                } else { // light i: its own weight, alias the current heavy
-                    const u128 dn = i + 1 < nl ? S.okey[swz(i + 1)] : D_tot;
-                    const u128 nq = Q - (dn - di);
-                    const uint32_t me = (uint32_t)(tile0 + S.ooff[i]);
-                    uint32_t alias = me;
-                    if (nq != Q) {
-                        if (j < nh) alias = (uint32_t)(tile0 + S.hoff[j]);
-                        else bad = true;
-                    }
-                    const uint64_t thr = lo64(nq >> shift);
-                    table[me] = make_uint4((uint32_t)thr, (uint32_t)(thr >> 32), alias, 0u);
-                    ++i;
-                    di = dn;
+    const uint32_t per = (M + kThreads - 1) / kThreads;
+    const uint32_t d0 = threadIdx.x * per;
+    if (d0 < M) {
+        uint32_t lo = d0 > A ? d0 - A : 0, hi = d0 < B ? d0 : B;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi + 1) >> 1;
+            if (S.hkey[swz(mid - 1)] <= S.okey[swz(d0 - mid)]) lo = mid; else hi = mid - 1;
+        }
+        uint32_t j = lo, i = d0 - lo;
+        const uint32_t steps = min(per, M - d0);
+        u128 ej = j < nh ? S.hkey[swz(j)] : (u128)0;
+        u128 di = i < nl ? S.okey[swz(i)] : D_tot;
+        for (uint32_t st = 0; st < steps; ++st) {
+            if ((j < B) && (i >= A || ej <= di)) { // heavy j: Q - (D_i - E_j), alias the next heavy (in the tile)
+                const u128 gap = di - ej;
+                if (gap > Q || j + 1 >= nh) bad = true;
+                const uint32_t me = (uint32_t)(tile0 + S.hoff[j]);
+                const uint32_t nx = (uint32_t)(tile0 + S.hoff[min(j + 1, nh - 1)]);
+                const uint32_t alias = gap == 0 ? me : nx;
+                const uint64_t thr = lo64((Q - gap) >> shift);
+                table[me] = make_uint4((uint32_t)thr, (uint32_t)(thr >> 32), alias, 0u);
+                ++j;
+                if (j < nh) ej = S.hkey[swz(j)];
+            } else { // light i: its own weight, alias the current heavy
+                const u128 dn = i + 1 < nl ? S.okey[swz(i + 1)] : D_tot;
+                const u128 nq = Q - (dn - di);
+                const uint32_t me = (uint32_t)(tile0 + S.ooff[i]);
+                uint32_t alias = me;
+                if (nq != Q) {
+                    if (j < nh) alias = (uint32_t)(tile0 + S.hoff[j]);
+                    else bad = true;
                 }
+                const uint64_t thr = lo64(nq >> shift);
+                table[me] = make_uint4((uint32_t)thr, (uint32_t)(thr >> 32), alias, 0u);
+                ++i;
+                di = dn;
             }
         }
     }
-    // the leftovers, in index order: lights of rank >= A, heavies of rank >= B
-    uint32_t left = 0;
+    // the leftovers' keys local to the tile, in its staging slots: lights
+    // first (D = deficits of the tile's leftover lights before), then heavies
+    // (E = excesses up to and including)
     {
         uint32_t lr = l0, hr = h0;
+        const uint64_t hbase = tile0 + ncl;
 #pragma unroll
         for (int k = 0; k < kItems; ++k) {
-            if ((lmask >> k) & 1u) { if (lr >= A) left |= 1u << k; ++lr; }
-            else if ((hmask >> k) & 1u) { if (hr >= B) left |= 1u << k; ++hr; }
-        }
-    }
-    uint32_t ntot;
-    uint32_t slot = block_exclusive_scan_u32((uint32_t)__popc(left), ntot, S.cnt);
-    {
-        uint32_t hr = h0;
-#pragma unroll
-        for (int k = 0; k < kItems; ++k) {
-            const bool is_h = (hmask >> k) & 1u;
-            if ((left >> k) & 1u) {
-                const u128 v = (is_h && hr == B) ? s_res : nq_of(x[k], F32, beta, n32);
-                lo_v[2 * (tile0 + slot)] = lo64(v);
-                lo_v[2 * (tile0 + slot) + 1] = hi64(v);
-                lo_idx[tile0 + slot] = (uint32_t)(first + k);
-                ++slot;
+            const uint32_t off = threadIdx.x * kItems + k;
+            if ((lmask >> k) & 1u) {
+                if (lr >= A) {
+                    const bool after = Bl && offB < off;
+                    const uint64_t pos = tile0 + (lr - A) + (after ? 1u : 0u);
+                    st_key(skeys + pos, S.okey[swz(lr)] - DA + (after ? Q - res : (u128)0));
+                    sidx[pos] = (uint32_t)(first + k);
+                }
+                ++lr;
+            } else if ((hmask >> k) & 1u) {
+                if (hr == B) {
+                    if (Bl) { // lr = the lights before it
+                        const u128 Dk = lr < nl ? S.okey[swz(lr)] : D_tot;
+                        const uint64_t pos = tile0 + (lr > A ? lr - A : 0u);
+                        st_key(skeys + pos, lr > A ? Dk - DA : (u128)0);
+                        sidx[pos] = (uint32_t)(first + k);
+                    } else {
+                        st_key(skeys + hbase, res - Q);
+                        sidx[hbase] = (uint32_t)(first + k);
+                    }
+                } else if (hr > B) {
+                    const uint64_t pos = hbase + (hr - B - 1) + (Bh ? 1u : 0u);
+                    st_key(skeys + pos, S.hkey[swz(hr)] - EB + (Bh ? res - Q : (u128)0));
+                    sidx[pos] = (uint32_t)(first + k);
+                }
+                ++hr;
             }
-            if (is_h) ++hr;
         }
-    }
-    if (threadIdx.x == 0) {
-        TileSum a;
-        a.l_lo = a.l_hi = a.h_lo = a.h_hi = 0;
-        a.cl = ntot; a.nheavy = 0; a.first_heavy = kNone; a.pad = 0;
-        tilesum_st(cnt_agg + blockIdx.x, a);
-        atomicAdd(reinterpret_cast<unsigned long long *>(&hdr->n_light), (unsigned long long)nl);
     }
     if (bad) set_status(hdr, kEInternal);
 }
 
-// -------------------------------------------------------- compaction
-// Tile t's leftovers (cnt_incl: inclusive prefix of the tiles' leftover
-// counts) move to [prefix before t, prefix through t) of the compacted list.
-__global__ void __launch_bounds__(kThreads) k_pp_compact(const uint64_t *__restrict__ lo_v,
-                                                         const uint32_t *__restrict__ lo_idx,
-                                                         const TileSum *__restrict__ cnt_incl,
-                                                         uint64_t *__restrict__ cv, uint32_t *__restrict__ cidx,
-                                                         const DevHeader *hdr)
+// ------------------------------------------------------- tile scan
+// Exclusive prefix of the tiles' leftover sums and counts, in two levels:
+// k_pp_scan1 scans 2048 tiles per block (tpre[t] = prefix within the block,
+// bsum[b] = the block's total); k_pp_scan2 (one block) turns bsum into
+// exclusive block prefixes and writes the grand total to tot.  n < 2^32
+// gives at most 2^21 tiles, so at most 1024 blocks.
+__device__ __forceinline__ void pp_scan_block(TileSum (&v)[kItems], uint32_t count, TileSum &total)
 {
-    if (*(volatile const uint32_t *)&hdr->status) return;
-    const uint32_t t = blockIdx.x;
-    const uint32_t end = tilesum_ldcg(cnt_incl + t).cl;
-    const uint32_t beg = t ? tilesum_ldcg(cnt_incl + t - 1).cl : 0u;
-    const uint64_t src = (uint64_t)t * kTile;
-    const uint4 *sv = reinterpret_cast<const uint4 *>(lo_v) + src;
-    uint4 *dv = reinterpret_cast<uint4 *>(cv) + beg;
-    for (uint32_t i = threadIdx.x; i < end - beg; i += kThreads) {
-        dv[i] = __ldcs(sv + i);
-        cidx[beg + i] = __ldcs(lo_idx + src + i);
+    __shared__ U2 s_scan[kWarps];
+    __shared__ uint32_t s_c1[kWarps], s_c2[kWarps];
+    TileSum sum = pp_zero();
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) pp_add(sum, v[k]);
+    U2 tot;
+    const U2 ex = block_exclusive_scan2(U2{mk128(sum.l_lo, sum.l_hi), mk128(sum.h_lo, sum.h_hi)}, tot, s_scan);
+    uint32_t t1, t2;
+    const uint32_t e1 = block_exclusive_scan_u32(sum.cl, t1, s_c1);
+    const uint32_t e2 = block_exclusive_scan_u32(sum.nheavy, t2, s_c2);
+    TileSum run;
+    run.l_lo = lo64(ex.a); run.l_hi = hi64(ex.a); run.h_lo = lo64(ex.b); run.h_hi = hi64(ex.b);
+    run.cl = e1; run.nheavy = e2; run.first_heavy = kNone; run.pad = 0;
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) { // v[k] becomes its exclusive prefix
+        const TileSum own = v[k];
+        v[k] = run;
+        pp_add(run, own);
+    }
+    total.l_lo = lo64(tot.a); total.l_hi = hi64(tot.a); total.h_lo = lo64(tot.b); total.h_hi = hi64(tot.b);
+    total.cl = t1; total.nheavy = t2; total.first_heavy = kNone; total.pad = 0;
+    (void)count;
+}
+
+__global__ void __launch_bounds__(kThreads) k_pp_scan1(const TileSum *__restrict__ tsum, uint32_t ntiles,
+                                                       const DevHeader *hdr, TileSum *__restrict__ tpre,
+                                                       TileSum *__restrict__ bsum)
+{
+    if (block_stopped(hdr)) return;
+    const uint64_t t0 = (uint64_t)blockIdx.x * kTile + (uint64_t)threadIdx.x * kItems;
+    TileSum v[kItems];
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) v[k] = t0 + k < ntiles ? tilesum_ldcg(tsum + t0 + k) : pp_zero();
+    TileSum total;
+    pp_scan_block(v, ntiles, total);
+#pragma unroll
+    for (int k = 0; k < kItems; ++k)
+        if (t0 + k < ntiles) tilesum_st(tpre + t0 + k, v[k]);
+    if (threadIdx.x == 0) tilesum_st(bsum + blockIdx.x, total);
+}
+
+__global__ void __launch_bounds__(kThreads) k_pp_scan2(TileSum *bsum, uint32_t nblocks, const DevHeader *hdr,
+                                                       TileSum *tot, uint32_t *m_out)
+{
+    if (block_stopped(hdr)) return;
+    const uint32_t b0 = threadIdx.x * kItems;
+    TileSum v[kItems];
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) v[k] = b0 + k < nblocks ? tilesum_ldcg(bsum + b0 + k) : pp_zero();
+    TileSum total;
+    pp_scan_block(v, nblocks, total);
+#pragma unroll
+    for (int k = 0; k < kItems; ++k)
+        if (b0 + k < nblocks) tilesum_st(bsum + b0 + k, v[k]);
+    if (threadIdx.x == 0) {
+        tilesum_st(tot, total);
+        *m_out = total.cl + total.nheavy;
     }
 }
 
-// Sets the leftover count m (from the scan of the tile counts) and rearms
-// the look-back scan's dynamic tile ids.
-__global__ void k_pp_reset(DevHeader *hdr, uint32_t *m_ptr, const TileSum *cnt_incl, uint32_t ntiles)
+// Tile t's staged keys plus the prefixes before the tile, moved to their
+// global ranks: light x of the tile to keys[L_before + x], heavy y to
+// keys[NL + H_before + y].  One warp per tile; coalesced on both sides.
+__global__ void __launch_bounds__(kThreads) k_pp_keys(const uint4 *__restrict__ skeys,
+                                                      const uint32_t *__restrict__ sidx,
+                                                      const TileSum *__restrict__ tsum,
+                                                      const TileSum *__restrict__ tpre,
+                                                      const TileSum *__restrict__ bsum, const TileSum *tot,
+                                                      uint32_t ntiles, const DevHeader *hdr,
+                                                      uint4 *__restrict__ keys, uint32_t *__restrict__ kidx)
 {
-    if (threadIdx.x == 0) {
-        hdr->tile_counter = 0;
-        *m_ptr = tilesum_ldcg(cnt_incl + (ntiles - 1)).cl;
+    if (*(volatile const uint32_t *)&hdr->status) return; // no barrier in this kernel
+    const uint32_t t = blockIdx.x * kWarps + (threadIdx.x >> 5);
+    if (t >= ntiles) return;
+    const uint32_t lane = threadIdx.x & 31;
+    const TileSum own = tilesum_ldcg(tsum + t);
+    const uint32_t cnt = own.cl + own.nheavy;
+    if (cnt == 0) return;
+    TileSum pre = tilesum_ldcg(bsum + t / kTile);
+    pp_add(pre, tilesum_ldcg(tpre + t));
+    const uint32_t NL = tilesum_ldcg(tot).cl;
+    const u128 D0 = mk128(pre.l_lo, pre.l_hi), E0 = mk128(pre.h_lo, pre.h_hi);
+    const uint64_t src = (uint64_t)t * kTile;
+    for (uint32_t x = lane; x < cnt; x += 32) {
+        const u128 k = ld_key(skeys + src + x);
+        const uint32_t idx = __ldcs(sidx + src + x);
+        uint64_t dst;
+        u128 key;
+        if (x < own.cl) { dst = (uint64_t)pre.cl + x; key = D0 + k; }
+        else { dst = (uint64_t)NL + pre.nheavy + (x - own.cl); key = E0 + k; }
+        st_key(keys + dst, key);
+        kidx[dst] = idx;
     }
 }
 
 // ------------------------------------------------------------ phase 2
-// Per tile of 2048 of the compacted list: its light count and the sums of
-// its lights' deficits Q - v and of its heavies' excesses v - Q (light iff
-// v <= Q).  Tiles past the list write zeros, so the scan's last inclusive
-// prefix holds the totals.
-__global__ void __launch_bounds__(kThreads) k_pp_tiles(const uint64_t *__restrict__ cv, const uint32_t *m_ptr,
-                                                       const DevHeader *hdr, TileSum *__restrict__ agg)
+// Totals of the leftovers: NL lights, NH heavies, D_tot deficits.
+struct PpTotals {
+    uint32_t NL, NH;
+    u128 D_tot;
+};
+
+__device__ __forceinline__ PpTotals pp_totals(const TileSum *tot)
 {
-    __shared__ U2 s_scan[kWarps];
-    __shared__ uint32_t s_cnt[kWarps];
-    if (block_stopped(hdr)) return;
-    const uint32_t m = *m_ptr;
-    const uint64_t t0 = (uint64_t)blockIdx.x * kTile;
-    const u128 Q = mk128(hdr->q_lo, hdr->q_hi);
-    const uint4 *v4 = reinterpret_cast<const uint4 *>(cv);
-    u128 sd = 0, se = 0;
-    uint32_t cl = 0;
-#pragma unroll
-    for (int k = 0; k < kItems; ++k) {
-        const uint64_t i = t0 + (uint64_t)k * kThreads + threadIdx.x; // order is irrelevant for sums
-        if (i < m) {
-            const uint4 r = __ldg(v4 + i);
-            const u128 v = mk128(r.x | ((uint64_t)r.y << 32), r.z | ((uint64_t)r.w << 32));
-            if (v <= Q) { sd += Q - v; ++cl; } else se += v - Q;
-        }
-    }
-    U2 tot;
-    block_exclusive_scan2(U2{sd, se}, tot, s_scan);
-    uint32_t ctot;
-    block_exclusive_scan_u32(cl, ctot, s_cnt);
-    if (threadIdx.x == 0) {
-        TileSum a;
-        a.l_lo = lo64(tot.a); a.l_hi = hi64(tot.a); a.h_lo = lo64(tot.b); a.h_hi = hi64(tot.b);
-        a.cl = ctot; a.nheavy = 0; a.first_heavy = kNone; a.pad = 0;
-        tilesum_st(agg + blockIdx.x, a);
-    }
+    const TileSum last = tilesum_ldcg(tot);
+    PpTotals t;
+    t.NL = last.cl;
+    t.NH = last.nheavy;
+    t.D_tot = mk128(last.l_lo, last.l_hi);
+    return t;
 }
 
-// Global keys of the leftovers, written once: the light of rank x at
-// keys[x] with D = the deficits of the lights before it, the heavy of rank y
-// at keys[NL + y] with E = the excesses of the heavies up to it (NL = the
-// light count), each key's item index beside it in kidx.
-__global__ void __launch_bounds__(kThreads) k_pp_keys(const uint64_t *__restrict__ cv,
-                                                      const uint32_t *__restrict__ cidx, const uint32_t *m_ptr,
-                                                      const DevHeader *hdr, const TileSum *__restrict__ incl,
-                                                      uint32_t ntiles, uint64_t *__restrict__ keys,
-                                                      uint32_t *__restrict__ kidx)
-{
-    __shared__ U2 s_scan[kWarps];
-    __shared__ uint32_t s_cnt[kWarps];
-    if (block_stopped(hdr)) return;
-    const uint32_t m = *m_ptr;
-    const uint64_t t0 = (uint64_t)blockIdx.x * kTile;
-    if (t0 >= m) return;
-    const u128 Q = mk128(hdr->q_lo, hdr->q_hi);
-    const uint32_t NL = tilesum_ldcg(incl + (ntiles - 1)).cl;
-    const TileSum before = load_prefix(incl, blockIdx.x);
-    const uint32_t heavies_before = (uint32_t)t0 - before.cl;
-    const uint64_t first = t0 + (uint64_t)threadIdx.x * kItems;
-    const uint4 *v4 = reinterpret_cast<const uint4 *>(cv);
-    u128 v[kItems];
-    u128 sd = 0, se = 0;
-    uint32_t cl = 0, ch = 0;
-#pragma unroll
-    for (int k = 0; k < kItems; ++k) {
-        v[k] = 0;
-        if (first + k < m) {
-            const uint4 r = __ldg(v4 + first + k);
-            v[k] = mk128(r.x | ((uint64_t)r.y << 32), r.z | ((uint64_t)r.w << 32));
-            if (v[k] <= Q) { sd += Q - v[k]; ++cl; } else { se += v[k] - Q; ++ch; }
-        }
-    }
-    U2 tot;
-    const U2 ex = block_exclusive_scan2(U2{sd, se}, tot, s_scan);
-    uint32_t ctot;
-    const uint32_t cex = block_exclusive_scan_u32(cl | (ch << 16), ctot, s_cnt);
-    u128 D = mk128(before.l_lo, before.l_hi) + ex.a, E = mk128(before.h_lo, before.h_hi) + ex.b;
-    uint64_t lr = before.cl + (cex & 0xFFFFu), hr = (uint64_t)NL + heavies_before + (cex >> 16);
-    uint4 *k4 = reinterpret_cast<uint4 *>(keys);
-#pragma unroll
-    for (int k = 0; k < kItems; ++k) {
-        if (first + k >= m) continue;
-        if (v[k] <= Q) {
-            k4[lr] = make_uint4((uint32_t)lo64(D), (uint32_t)(lo64(D) >> 32), (uint32_t)hi64(D),
-                                (uint32_t)(hi64(D) >> 32));
-            kidx[lr] = cidx[first + k];
-            D += Q - v[k];
-            ++lr;
-        } else {
-            E += v[k] - Q;
-            k4[hr] = make_uint4((uint32_t)lo64(E), (uint32_t)(lo64(E) >> 32), (uint32_t)hi64(E),
-                                (uint32_t)(hi64(E) >> 32));
-            kidx[hr] = cidx[first + k];
-            ++hr;
-        }
-    }
-}
+constexpr uint32_t kMergeSteps = 1024; // merge steps per block of k_pp_merge
 
-__device__ __forceinline__ u128 pp_key(const uint64_t *keys, uint64_t i)
+// Where merge block b starts: the number j of heavies among the first d =
+// 1024 b merged items, the largest j in [max(0, d - NL), min(d, NH)] that is
+// its lower end or has heavy j-1 before light d-j (E[j-1] <= D[d-j]).  The
+// predicate holds for every j up to the answer and for none after it.  One
+// warp per block: each round probes 32 evenly spaced candidates, so m keys
+// take about log_32(m) rounds.  starts[b] = (lights, heavies) before it.
+__global__ void __launch_bounds__(kThreads) k_pp_starts(const uint4 *__restrict__ keys, const DevHeader *hdr,
+                                                        const TileSum *tot, uint2 *__restrict__ starts)
 {
-    const uint4 r = __ldcg(reinterpret_cast<const uint4 *>(keys) + i);
-    return mk128(r.x | ((uint64_t)r.y << 32), r.z | ((uint64_t)r.w << 32));
+    if (*(volatile const uint32_t *)&hdr->status) return; // no barrier in this kernel
+    const PpTotals T = pp_totals(tot);
+    const uint64_t m = (uint64_t)T.NL + T.NH;
+    const uint4 *lkeys = keys, *hkeys = keys + T.NL;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t b = (uint64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+    const uint64_t d = b * kMergeSteps;
+    if (d >= m) return;
+    uint64_t lo = d > T.NL ? d - T.NL : 0, hi = d < T.NH ? d : T.NH;
+    while (lo < hi) {
+        const uint64_t step = (hi - lo + 31) / 32;
+        const uint64_t p = lo + 1 + step * lane;
+        bool ok = false;
+        if (p <= hi) ok = (d - p >= T.NL) || ld_key(hkeys + (p - 1)) <= ld_key(lkeys + (d - p));
+        const uint32_t cnt = (uint32_t)__popc(__ballot_sync(0xFFFFFFFFu, ok));
+        if (cnt == 0) break;
+        const uint64_t nhi = lo + step * cnt; // the first failing probe, minus one
+        lo = lo + 1 + step * (cnt - 1);
+        hi = nhi < hi ? nhi : hi;
+    }
+    if (lane == 0) starts[b] = make_uint2((uint32_t)(d - lo), (uint32_t)lo);
 }
 
 struct PpSmem {
-    u128 lkey[kTile + 8];   // keys D of the lights the block may reach (swizzled)
-    u128 hkey[kTile + 8];   // keys E of the heavies it may reach (swizzled)
-    uint32_t lidx[kTile + 1];
-    uint32_t hidx[kTile + 2];
-    uint32_t start[2];
+    u128 lkey[kMergeSteps + 8];   // keys D of the lights the block may reach (swizzled)
+    u128 hkey[kMergeSteps + 8];   // keys E of the heavies it may reach (swizzled)
+    uint32_t lidx[kMergeSteps + 1];
+    uint32_t hidx[kMergeSteps + 2];
 };
 
-// Block b walks merge steps [2048 b, 2048 (b + 1)) of the leftovers' lights
+// Block b walks merge steps [1024 b, 1024 (b + 1)) of the leftovers' lights
 // (keys D) and heavies (keys E), a heavy before a light when E <= D: a
 // light's bucket is its own v with the current heavy as alias; a heavy's is
 // Q - (D_next - E) with D_next the key of the next light, and the next heavy
-// as alias (itself when the bucket is full).  The block's first step is
-// found by a co-rank search over the global keys, done by one warp: each
-// round probes 32 evenly spaced candidates, so a list of m keys takes about
-// log_32(m) rounds.
-__global__ void __launch_bounds__(kThreads) k_pp_merge(const uint64_t *__restrict__ keys,
-                                                       const uint32_t *__restrict__ kidx, const uint32_t *m_ptr,
-                                                       DevHeader *hdr, const TileSum *__restrict__ incl,
-                                                       uint32_t ntiles, uint4 *__restrict__ table)
+// as alias (itself when the bucket is full).
+__global__ void __launch_bounds__(kThreads) k_pp_merge(const uint4 *__restrict__ keys,
+                                                       const uint32_t *__restrict__ kidx, DevHeader *hdr,
+                                                       const TileSum *tot, const uint2 *__restrict__ starts,
+                                                       uint4 *__restrict__ table)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PpSmem &S = *reinterpret_cast<PpSmem *>(smem_raw);
     if (block_stopped(hdr)) return;
-    const uint32_t m = *m_ptr;
-    const uint64_t d_begin = (uint64_t)blockIdx.x * kTile;
+    const PpTotals T = pp_totals(tot);
+    const uint64_t m = (uint64_t)T.NL + T.NH;
+    const uint64_t d_begin = (uint64_t)blockIdx.x * kMergeSteps;
     if (d_begin >= m) return;
-    const uint32_t steps_total = (uint32_t)min((uint64_t)kTile, (uint64_t)m - d_begin);
+    const uint4 *lkeys = keys, *hkeys = keys + T.NL;
+    const uint32_t *lidx = kidx, *hidx = kidx + T.NL;
+    const uint32_t steps_total = (uint32_t)min((uint64_t)kMergeSteps, m - d_begin);
     const u128 Q = mk128(hdr->q_lo, hdr->q_hi);
     const uint32_t shift = hdr->shift;
-    const TileSum last = tilesum_ldcg(incl + (ntiles - 1));
-    const uint32_t NL = last.cl, NH = m - last.cl;
-    const u128 D_tot = mk128(last.l_lo, last.l_hi);
-    const uint64_t *lkeys = keys, *hkeys = keys + 2 * (uint64_t)NL;
-    // co-rank of step d: the number j of heavies among the first d merged
-    // items, the largest j in [max(0, d - NL), min(d, NH)] with j = its lower
-    // end or heavy j-1 before light d-j (E[j-1] <= D[d-j]); the predicate
-    // holds for every j up to the answer and for none after it
-    if (threadIdx.x < 32) {
-        const uint32_t lane = threadIdx.x;
-        const uint64_t d = d_begin;
-        uint64_t lo = d > NL ? d - NL : 0, hi = d < NH ? d : NH;
-        while (lo < hi) {
-            const uint64_t step = (hi - lo + 31) / 32;
-            const uint64_t p = lo + 1 + step * lane;
-            bool ok = false;
-            if (p <= hi) ok = (d - p >= NL) || pp_key(hkeys, p - 1) <= pp_key(lkeys, d - p);
-            const uint32_t cnt = (uint32_t)__popc(__ballot_sync(0xFFFFFFFFu, ok));
-            if (cnt == 0) break;
-            const uint64_t nhi = lo + step * cnt; // the first failing probe, minus one
-            lo = lo + 1 + step * (cnt - 1);
-            hi = nhi < hi ? nhi : hi;
-        }
-        if (lane == 0) { S.start[0] = (uint32_t)(d - lo); S.start[1] = (uint32_t)lo; }
+    const uint2 st0 = starts[blockIdx.x];
+    const uint32_t i0 = st0.x, j0 = st0.y;
+    // the block consumes the keys up to the next block's start; one more of
+    // each kind is read as the "next" key
+    uint32_t i1 = T.NL, j1 = T.NH;
+    if (d_begin + kMergeSteps < m) {
+        const uint2 st1 = starts[blockIdx.x + 1];
+        i1 = st1.x;
+        j1 = st1.y;
     }
-    __syncthreads();
-    const uint32_t i0 = S.start[0], j0 = S.start[1];
-    // the block consumes at most steps_total keys of either kind; one more of
-    // each is read as the "next" key
-    const uint32_t la = (uint32_t)min((uint64_t)steps_total + 1, (uint64_t)(NL - i0));
-    const uint32_t hb = (uint32_t)min((uint64_t)steps_total + 1, (uint64_t)(NH - j0));
+    const uint32_t la = min(i1 - i0 + 1, T.NL - i0);
+    const uint32_t hb = min(j1 - j0 + 1, T.NH - j0);
     for (uint32_t t = threadIdx.x; t < la; t += kThreads) {
-        S.lkey[swz(t)] = pp_key(lkeys, (uint64_t)i0 + t);
-        S.lidx[t] = kidx[(uint64_t)i0 + t];
+        S.lkey[swz(t)] = ld_key(lkeys + (uint64_t)i0 + t);
+        S.lidx[t] = lidx[(uint64_t)i0 + t];
     }
     for (uint32_t t = threadIdx.x; t < hb; t += kThreads) {
-        S.hkey[swz(t)] = pp_key(hkeys, (uint64_t)j0 + t);
-        S.hidx[t] = kidx[(uint64_t)NL + j0 + t];
+        S.hkey[swz(t)] = ld_key(hkeys + (uint64_t)j0 + t);
+        S.hidx[t] = hidx[(uint64_t)j0 + t];
     }
-    if (threadIdx.x == 0) S.hidx[hb] = ((uint64_t)j0 + hb < NH) ? kidx[(uint64_t)NL + j0 + hb] : kNone;
+    if (threadIdx.x == 0) S.hidx[hb] = ((uint64_t)j0 + hb < T.NH) ? hidx[(uint64_t)j0 + hb] : kNone;
     __syncthreads();
     // the block's steps, split evenly over the threads by a local co-rank
     // search (light i of the block is global light i0 + i; past the loaded
@@ -428,7 +483,7 @@ __global__ void __launch_bounds__(kThreads) k_pp_merge(const uint64_t *__restric
         uint32_t j = lo, i = d0 - lo;
         const uint32_t steps = min(per, steps_total - d0);
         for (uint32_t st = 0; st < steps; ++st) {
-            const u128 di = i < la ? S.lkey[swz(i)] : D_tot;
+            const u128 di = i < la ? S.lkey[swz(i)] : T.D_tot;
             if (j < hb && (i >= la || S.hkey[swz(j)] <= di)) { // heavy j
                 const u128 gap = di - S.hkey[swz(j)];
                 const uint32_t me = S.hidx[j], nx = S.hidx[j + 1];
@@ -440,12 +495,13 @@ __global__ void __launch_bounds__(kThreads) k_pp_merge(const uint64_t *__restric
             } else { // light i
                 if (i >= la) { bad = true; break; }
                 const u128 dn = (i + 1 < la) ? S.lkey[swz(i + 1)]
-                                             : ((uint64_t)i0 + i + 1 < NL ? pp_key(lkeys, (uint64_t)i0 + i + 1) : D_tot);
+                                             : ((uint64_t)i0 + i + 1 < T.NL ? ld_key(lkeys + (uint64_t)i0 + i + 1)
+                                                                            : T.D_tot);
                 const u128 v = Q - (dn - di);
                 const uint32_t me = S.lidx[i];
                 uint32_t alias = me;
                 if (v != Q) {
-                    if ((uint64_t)j0 + j < NH) alias = j < hb ? S.hidx[j] : kidx[(uint64_t)NL + j0 + j];
+                    if ((uint64_t)j0 + j < T.NH) alias = j < hb ? S.hidx[j] : hidx[(uint64_t)j0 + j];
                     else bad = true;
                 }
                 const uint64_t thr = lo64(v >> shift);
@@ -479,21 +535,30 @@ wrs_status psa_plus_attributes()
     return WRS_OK;
 }
 
-// PSA+ scratch of a table, 40 bytes per weight of capacity: the per-tile
-// leftovers (value, index), the compacted list (value, index) -- the global
-// keys reuse the first pair -- and the leftover count.
+// PSA+ scratch of a table, about 40 bytes per weight of capacity: staged
+// keys and item indices of the leftovers (tile by tile), the same at their
+// global ranks, per-tile leftover sums and their prefixes, block sums, the
+// totals, merge-block starts and the leftover count.
 struct PpLayout {
-    uint64_t lo_v, lo_idx, cv, cidx, m, total;
+    uint64_t skeys, sidx, keys, kidx, tsum, tpre, bsum, tot, starts, m, total;
 };
 
 PpLayout pp_layout(uint64_t cap)
 {
+    const uint64_t ntiles = (cap + kTile - 1) / kTile;
+    const uint64_t nblocks = (ntiles + kTile - 1) / kTile;
+    const uint64_t nmerge = (cap + kMergeSteps - 1) / kMergeSteps;
     PpLayout L;
     uint64_t o = 0;
-    L.lo_v = o; o = align_up(o + cap * 16, 256);
-    L.lo_idx = o; o = align_up(o + cap * 4, 256);
-    L.cv = o; o = align_up(o + cap * 16, 256);
-    L.cidx = o; o = align_up(o + cap * 4, 256);
+    L.skeys = o; o = align_up(o + ntiles * kTile * 16, 256);
+    L.sidx = o; o = align_up(o + ntiles * kTile * 4, 256);
+    L.keys = o; o = align_up(o + cap * 16, 256);
+    L.kidx = o; o = align_up(o + cap * 4, 256);
+    L.tsum = o; o = align_up(o + ntiles * sizeof(TileSum), 256);
+    L.tpre = o; o = align_up(o + ntiles * sizeof(TileSum), 256);
+    L.bsum = o; o = align_up(o + nblocks * sizeof(TileSum), 256);
+    L.tot = o; o = align_up(o + sizeof(TileSum), 256);
+    L.starts = o; o = align_up(o + nmerge * sizeof(uint2), 256);
     L.m = o; o = align_up(o + 16, 256);
     L.total = o;
     return L;
@@ -513,49 +578,50 @@ wrs_status wrs_table_build_psa_plus(wrs_table *t, const void *d_weights, uint64_
     const PpLayout L = pp_layout(t->cap);
     if (!t->pp_ws) {
         cudaError_t e = cudaMalloc(&t->pp_ws, L.total);
-        if (e != cudaSuccess) { t->pp_ws = nullptr; return cuda_err(e); }
+        if (e != cudaSuccess) {
+            t->pp_ws = nullptr;
+            return cuda_err(e);
+        }
     }
-    uint64_t *lo_v = reinterpret_cast<uint64_t *>(t->pp_ws + L.lo_v);
-    uint32_t *lo_idx = reinterpret_cast<uint32_t *>(t->pp_ws + L.lo_idx);
-    uint64_t *cv = reinterpret_cast<uint64_t *>(t->pp_ws + L.cv);
-    uint32_t *cidx = reinterpret_cast<uint32_t *>(t->pp_ws + L.cidx);
-    uint32_t *m = reinterpret_cast<uint32_t *>(t->pp_ws + L.m);
+    uint8_t *ws = t->pp_ws;
+    uint4 *skeys = reinterpret_cast<uint4 *>(ws + L.skeys);
+    uint32_t *sidx = reinterpret_cast<uint32_t *>(ws + L.sidx);
+    uint4 *keys = reinterpret_cast<uint4 *>(ws + L.keys);
+    uint32_t *kidx = reinterpret_cast<uint32_t *>(ws + L.kidx);
+    TileSum *tsum = reinterpret_cast<TileSum *>(ws + L.tsum);
+    TileSum *tpre = reinterpret_cast<TileSum *>(ws + L.tpre);
+    TileSum *bsum = reinterpret_cast<TileSum *>(ws + L.bsum);
+    TileSum *tot = reinterpret_cast<TileSum *>(ws + L.tot);
+    uint2 *starts = reinterpret_cast<uint2 *>(ws + L.starts);
+    uint32_t *m = reinterpret_cast<uint32_t *>(ws + L.m);
 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const uint32_t *w = static_cast<const uint32_t *>(d_weights);
     const int vec = (reinterpret_cast<uintptr_t>(w) % 16) == 0;
     const uint32_t f32 = dtype == WRS_F32;
     const uint32_t ntiles = (uint32_t)((n + kTile - 1) / kTile);
-    const uint32_t nchunks = (ntiles + kScanChunk - 1) / kScanChunk;
+    const uint32_t nblocks = (ntiles + kTile - 1) / kTile;
+    const uint32_t nmerge = (uint32_t)((n + kMergeSteps - 1) / kMergeSteps);
     uint64_t want = (n + (uint64_t)kThreads * 16 - 1) / ((uint64_t)kThreads * 16);
     uint32_t nparts = (uint32_t)(want < 1 ? 1 : (want > kMaxParts ? kMaxParts : want));
     const uint32_t blocks_cap = (uint32_t)sm_count() * 8;
     if (nparts > blocks_cap) nparts = blocks_cap;
-    const uint32_t wait_limit = g_wait_limit.load();
-    uint32_t epoch[2];
-    for (int i = 0; i < 2; ++i) {
-        t->epoch = t->epoch + 1;
-        if (t->epoch >= (1u << 30)) t->epoch = 1;
-        epoch[i] = t->epoch;
-    }
 
     // Q, beta, light_max (the weight-total pass of PSA)
     if (f32) k_stats<1><<<nparts, kThreads, 0, s>>>(w, n, vec, t->part);
     else k_stats<0><<<nparts, kThreads, 0, s>>>(w, n, vec, t->part);
     k_stats_combine<<<1, kThreads, 0, s>>>(t->part, nparts, n, f32, t->hdr);
-    // phase 1: greedy per tile; leftover counts into agg
-    if (f32) k_pp_local<1><<<ntiles, kThreads, sizeof(GroupSmem), s>>>(w, n, vec, t->hdr, t->buckets, lo_v, lo_idx, t->agg);
-    else k_pp_local<0><<<ntiles, kThreads, sizeof(GroupSmem), s>>>(w, n, vec, t->hdr, t->buckets, lo_v, lo_idx, t->agg);
-    k_tilescan<<<nchunks, kThreads, 0, s>>>(t->hdr, t->agg, t->cagg, t->cincl, t->incl, t->flags, ntiles, epoch[0],
-                                            wait_limit, kNone);
-    k_pp_compact<<<ntiles, kThreads, 0, s>>>(lo_v, lo_idx, t->incl, cv, cidx, t->hdr);
-    k_pp_reset<<<1, 32, 0, s>>>(t->hdr, m, t->incl, ntiles);
-    // phase 2: Alg. 2 on the leftovers (their keys overwrite lo_v / lo_idx)
-    k_pp_tiles<<<ntiles, kThreads, 0, s>>>(cv, m, t->hdr, t->agg);
-    k_tilescan<<<nchunks, kThreads, 0, s>>>(t->hdr, t->agg, t->cagg, t->cincl, t->incl, t->flags, ntiles, epoch[1],
-                                            wait_limit, kNone);
-    k_pp_keys<<<ntiles, kThreads, 0, s>>>(cv, cidx, m, t->hdr, t->incl, ntiles, lo_v, lo_idx);
-    k_pp_merge<<<ntiles, kThreads, sizeof(PpSmem), s>>>(lo_v, lo_idx, m, t->hdr, t->incl, ntiles, t->buckets);
+    // phase 1; the leftovers' local keys and per-tile sums
+    const size_t gs = sizeof(GroupSmem);
+    if (f32) k_pp_local<1><<<ntiles, kThreads, gs, s>>>(w, n, vec, t->hdr, t->buckets, tsum, skeys, sidx);
+    else k_pp_local<0><<<ntiles, kThreads, gs, s>>>(w, n, vec, t->hdr, t->buckets, tsum, skeys, sidx);
+    // phase 2: Alg. 2 on the leftovers
+    k_pp_scan1<<<nblocks, kThreads, 0, s>>>(tsum, ntiles, t->hdr, tpre, bsum);
+    k_pp_scan2<<<1, kThreads, 0, s>>>(bsum, nblocks, t->hdr, tot, m);
+    k_pp_keys<<<(ntiles + kWarps - 1) / kWarps, kThreads, 0, s>>>(skeys, sidx, tsum, tpre, bsum, tot, ntiles, t->hdr,
+                                                                 keys, kidx);
+    k_pp_starts<<<(nmerge + kWarps - 1) / kWarps, kThreads, 0, s>>>(keys, t->hdr, tot, starts);
+    k_pp_merge<<<nmerge, kThreads, sizeof(PpSmem), s>>>(keys, kidx, t->hdr, tot, starts, t->buckets);
     st = launch_err();
     if (st == WRS_OK) {
         t->n = n;
