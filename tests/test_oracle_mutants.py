@@ -9,6 +9,7 @@ import pytest
 
 from oracle import wrs_oracle as O
 from tests import test_oracle_pins as P
+from tests import test_oracle_psaplus as PP
 
 SRC = os.path.join(os.path.dirname(O.__file__), "wrs_oracle.c")
 
@@ -57,6 +58,53 @@ PINS = [
     P.test_sampler_tails_take_the_alias,
     P.test_sampler_coin_with_small_denominator,
 ]
+
+
+# PSA+ (Sec. 4.2 "Performance Optimization in Practice"), caught by the PSA+ pins
+PP_MUTANTS = {
+    # the heavy item current at the stop is handed on whole instead of with its residual
+    "pp_residual_dropped": ("            st128(lv + 2 * m, k == cur ? w : nq(&in, k));",
+                            "            st128(lv + 2 * m, nq(&in, k));"),
+    # a heavy item at or under capacity with no next heavy in the tile is finished in place
+    "pp_finish_in_place": ("                    if (jn >= t1) break;\n                    put(bw, al, j, w, jn);",
+                           "                    if (jn >= t1) { put(bw, al, j, w, j); done[j - t0] = 1; break; }\n"
+                           "                    put(bw, al, j, w, jn);"),
+    # a packed heavy item's overflow goes to itself instead of the next heavy item
+    "pp_heavy_alias_self": ("                    put(bw, al, j, w, jn);\n                    done[j - t0] = 1;",
+                            "                    put(bw, al, j, w, j);\n                    done[j - t0] = 1;"),
+}
+
+
+def _pp_alias_tables():
+    for name, w in PP.INPUTS[:4]:
+        for T in (3, 64):
+            PP.test_every_tile_size_gives_an_alias_table(name, w, T)
+
+
+PP_PINS = [PP.test_hand_examples, PP.test_exhaustive_small, _pp_alias_tables]
+
+
+def _run_mutant(old, new, pins, tmp_path):
+    src = open(SRC).read()
+    assert src.count(old) == 1, "mutation site not found exactly once"
+    mutated = tmp_path / "mutant.c"
+    mutated.write_text(src.replace(old, new))
+    so = str(tmp_path / "libmutant.so")
+    subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-o", so, str(mutated), "-lm"])
+    caught = []
+    with O.use_library(so):
+        for pin in pins:
+            try:
+                pin()
+            except Exception:  # a failed assertion or an oracle error both count as caught
+                caught.append(pin.__name__)
+    return caught
+
+
+@pytest.mark.parametrize("name", sorted(PP_MUTANTS))
+def test_every_planted_psa_plus_mistake_is_caught(name, tmp_path):
+    old, new = PP_MUTANTS[name]
+    assert _run_mutant(old, new, PP_PINS, tmp_path), f"mutant {name} passed every PSA+ pin"
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))

@@ -66,3 +66,25 @@ def test_greedy_phase_leaves_few_items_on_uniform_inputs():
     qz = O.quantize(WL.f32_uniform(200_000, 9))
     _, left = O.psa_plus(qz, 2048, return_left=True)
     assert left < 0.05 * qz.n
+
+
+def test_hand_examples():
+    """Tables worked by hand from the PSA+ rule (tests/golden/
+    psa_plus_hand_examples.json): buckets, leftover count, and, for the first
+    example, a table different from Alg. 2's on the same weights."""
+    import json
+    import os
+
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "psa_plus_hand_examples.json")))
+    for ex in g["examples"]:
+        w = np.array(ex["w"], np.uint32)
+        qz = O.quantize(w)
+        assert qz.Q == ex["Q"]
+        t, n_left = O.psa_plus(qz, ex["T"], return_left=True)
+        want = np.array(ex["psa_plus"], np.uint64)
+        assert np.array_equal(t.thr, want[:, 0]) and np.array_equal(t.alias, want[:, 1].astype(np.uint32)), ex["name"]
+        assert n_left == ex["n_left"]
+        _, ref = O.build_table(w)
+        a2 = np.array(ex["alg2"], np.uint64)
+        assert np.array_equal(ref.thr, a2[:, 0]) and np.array_equal(ref.alias, a2[:, 1].astype(np.uint32))
+    assert g["examples"][0]["psa_plus"] != g["examples"][0]["alg2"]
