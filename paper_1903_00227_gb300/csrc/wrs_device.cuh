@@ -157,6 +157,16 @@ __device__ __forceinline__ void set_status(DevHeader *h, uint32_t code)
     atomicCAS(&h->status, 0u, code);
 }
 
+// The table's status, read once for the whole block: every thread returns
+// or none does, so no later block barrier waits for threads that left.
+__device__ __forceinline__ bool block_stopped(const DevHeader *hdr)
+{
+    __shared__ uint32_t s_status_word;
+    if (threadIdx.x == 0) s_status_word = *(volatile const uint32_t *)&hdr->status;
+    __syncthreads();
+    return s_status_word != 0;
+}
+
 // --------------------------------------------------------- block scans
 // Exclusive scan of a u32 over the block (all threads call; uses sm[kWarps]).
 __device__ __forceinline__ uint32_t block_exclusive_scan_u32(uint32_t v, uint32_t &total, uint32_t *sm)

@@ -335,7 +335,7 @@ __device__ __forceinline__ void classify_body(const uint32_t *__restrict__ w, ui
     __shared__ u128 s_l[kWarps], s_h[kWarps];
     __shared__ uint32_t s_c[kWarps], s_first[kWarps];
     __shared__ uint32_t s_cnt[kWarps];
-    if (*(volatile const uint32_t *)&hdr->status) return;
+    if (block_stopped(hdr)) return;
     const uint32_t light_max = hdr->light_max;
     const int beta = hdr->beta;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -807,7 +807,7 @@ __device__ __forceinline__ void sweep_body(const uint32_t *__restrict__ w, uint6
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SweepSmem &S = *reinterpret_cast<SweepSmem *>(smem_raw);
-    if (*(volatile uint32_t *)&hdr->status) return;
+    if (block_stopped(hdr)) return;
     const uint32_t n32 = (uint32_t)n;
     const u128 Q = mk128(hdr->q_lo, hdr->q_hi);
     const uint32_t light_max = hdr->light_max;

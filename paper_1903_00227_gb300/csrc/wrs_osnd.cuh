@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(kThreads) k_os_level(const void *__restrict__ 
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     OsSmem &S = *reinterpret_cast<OsSmem *>(smem_raw);
-    if (*(volatile uint32_t *)&hdr->status) return;
+    if (block_stopped(hdr)) return;
     const int beta = hdr->beta;
     const uint64_t nf = *nfront;
     for (uint64_t e = blockIdx.x; e < nf; e += gridDim.x) {
@@ -382,7 +382,8 @@ __global__ void __launch_bounds__(256) k_os_small0(uint64_t N, const uint4 *__re
                                                    unsigned long long *nout, uint64_t cap, uint64_t seed,
                                                    uint64_t stream)
 {
-    if (*(volatile const uint32_t *)&hdr->status) return;
+    // one read per warp: its lanes leave together (warp collectives follow)
+    if (__shfl_sync(0xFFFFFFFFu, *(volatile const uint32_t *)&hdr->status, 0)) return;
     const uint64_t nf = *nfront;
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;

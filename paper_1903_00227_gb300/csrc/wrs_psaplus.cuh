@@ -27,16 +27,6 @@
 
 namespace wrs {
 
-// The table's status, read once for the whole block (every thread returns or
-// none does, so no later barrier is left waiting).
-__device__ __forceinline__ bool block_stopped(const DevHeader *hdr)
-{
-    __shared__ uint32_t s_st;
-    if (threadIdx.x == 0) s_st = *(volatile const uint32_t *)&hdr->status;
-    __syncthreads();
-    return s_st != 0;
-}
-
 // Leftover sums of tiles: l = deficits of the lights (v <= Q), h = excesses
 // of the heavies, cl / nheavy = their counts (TileSum's fields).
 __device__ __forceinline__ void pp_add(TileSum &a, const TileSum &b)

@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(kThreads, 3) k2_group(const void *__restrict__
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     GroupSmem &S = *reinterpret_cast<GroupSmem *>(smem_raw);
-    if (*(volatile uint32_t *)&hdr->status) return;
+    if (block_stopped(hdr)) return;
     const int beta = hdr->beta;
     const uint64_t base = (uint64_t)blockIdx.x * kTile;
     const uint32_t ng = (uint32_t)min((uint64_t)kTile, N - base);
