@@ -17,11 +17,24 @@ pytestmark = pytest.mark.gpu
 N = int(os.environ.get("WRS_FULLSIZE_N", 10 ** 9))
 
 
-def test_full_size_table_and_samples():
+@pytest.mark.parametrize("builder", ["psa", "psa_plus"])
+def test_full_size_table_and_samples(builder):
+    """PSA (Alg. 3, the bench's headline build) and PSA+ (Sec. 4.2, per-tile
+    greedy packing, then PSA on the leftovers) on the same 10^9 weights: both
+    must be alias tables of the weights (light buckets hold their own weight,
+    every alias is a heavy item or the bucket itself, the pieces of every item
+    add up to n*q exactly), and 10^5 of 10^9 samples must equal the oracle's
+    queries of the downloaded table."""
     w = WL.generate_device("f32_uniform", N, 7)
     table = wrs.AliasTable(N)
-    table.build(w)
+    if builder == "psa":
+        table.build(w)
+    else:
+        table.build_psa_plus(w)
     assert table.status() == wrs.OK
+    if builder == "psa_plus":
+        left = table.psa_plus_leftovers()
+        assert 0 < left < N // 10  # uniform weights: the tiles pack almost everything themselves
     info = table.info()
     assert info.shift == 0 and info.qp < 2 ** 62  # Q < 2^62 for these weights: int64 arithmetic below is exact
     host = np.empty(2 * N, dtype=np.uint64)
