@@ -12,7 +12,8 @@ steps.
 Printed JSON line (rank 0): ``value`` is the build throughput over all ranks
 in Gweights/s; ``sample`` gives the sampling throughput; ``e2e`` repeats the
 step through the C ABI's host-buffer entry points with the host<->device
-copies inside the timed region; ``roofline`` is the dominant kernel against
+copies inside the timed region (two table objects double-buffered; the
+serial one-table figure beside it); ``roofline`` is the dominant kernel against
 the measured HBM copy bandwidth; ``cpu_baseline`` times the CPU oracle on a
 bounded sample of the same workload.
 
@@ -531,6 +532,86 @@ def run_serving(args, torch):
     return out
 
 
+def run_e2e(args, torch, wrs, table, weights, names, stream, ws):
+    """The step through the C ABI's host-buffer entry points, with every host
+    <-> device copy inside the timed region: wrs_table_build_host uploads
+    the step's weights from pinned memory and builds, wrs_sample_host draws k
+    samples and returns them in pinned memory.  `value`: a stream of steps on
+    two table objects and two CUDA streams, step i+1's upload and build
+    issued before step i's sampling (double buffering: the link carries one
+    step's weights while the GPU samples the other's table).  `serial`: one
+    table, one step at a time."""
+    n, k = args.n, args.k
+    K = args.e2e_steps
+    h_in = {}
+    for name in names:  # each distribution's weights in pinned host memory (prepared once, untimed)
+        h_in[name] = torch.empty(n, dtype=torch.float32, pin_memory=True)
+        h_in[name].copy_(weights[name])
+    h_out = [torch.empty(k, dtype=torch.int32, pin_memory=True) for _ in range(2)]
+    torch.cuda.synchronize()
+
+    def build_host(t, name, sh):
+        rc = wrs.table_build_host(t.handle, h_in[name].data_ptr(), n, wrs.F32, sh)
+        assert rc == wrs.OK, wrs.status_str(rc)
+
+    def sample_host(t, i, slot, sh):
+        rc = wrs.sample_host(t.handle, k, 5000 + i, 0, h_out[slot].data_ptr(), sh)
+        assert rc == wrs.OK, wrs.status_str(rc)
+
+    # serial: one table, one step at a time (first call allocates the staging buffers)
+    sh0 = stream.cuda_stream
+    times = []
+    for i in range(K + 1):
+        name = names[i % len(names)]
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        build_host(table, name, sh0)
+        sample_host(table, i, 0, sh0)
+        e1.record(stream)
+        e1.synchronize()
+        if i > 0:
+            times.append(e0.elapsed_time(e1))
+    t_serial = reduce_max([statistics.mean(times)], "cuda")[0]
+
+    # pipelined: two table objects on two streams
+    tables = [table, wrs.AliasTable(n)]
+    streams = [stream, torch.cuda.Stream()]
+    shs = [x.cuda_stream for x in streams]
+    build_host(tables[1], names[0], shs[1])  # warm-up: staging buffers of the second object
+    sample_host(tables[1], 0, 1, shs[1])
+    torch.cuda.synchronize()
+    steps = max(2 * K, 6)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(streams[0])
+    streams[1].wait_event(e0)
+    build_host(tables[0], names[0], shs[0])
+    for i in range(steps):
+        cur, nxt = i % 2, (i + 1) % 2
+        if i + 1 < steps:
+            build_host(tables[nxt], names[(i + 1) % len(names)], shs[nxt])
+        sample_host(tables[cur], i, cur, shs[cur])  # returns with the samples in host memory
+    done = torch.cuda.Event()
+    done.record(streams[1])
+    streams[0].wait_event(done)
+    e1.record(streams[0])
+    e1.synchronize()
+    t_pipe = reduce_max([e0.elapsed_time(e1) / steps], "cuda")[0]
+    for t in tables:
+        if t.status() != wrs.OK:
+            raise RuntimeError("end-to-end build failed")
+    tables[1].free()
+    del h_in, h_out
+    return {"value": ws * n / (t_pipe * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": 4 * n,
+            "d2h_bytes_per_step": 4 * k, "ms_per_step": t_pipe, "steps": steps,
+            "serial": {"value": ws * n / (t_serial * 1e-3) / 1e9, "ms_per_step": t_serial},
+            "note": "wrs_table_build_host (H2D of the weights) + wrs_sample_host (D2H of the samples) per step; "
+                    "two table objects and two streams, step i+1's upload and build issued before step i's "
+                    "sampling; serial = one table, one step at a time"}
+
+
 def run_ours(args, names):
     import torch
 
@@ -653,28 +734,7 @@ def run_ours(args, names):
     # end to end through the C ABI with host buffers (copies inside the timed region)
     e2e = None
     if args.e2e_steps > 0:
-        h_w = torch.empty(n, dtype=torch.float32, pin_memory=True)
-        h_out = torch.empty(k, dtype=torch.int32, pin_memory=True)
-        times = []
-        for i in range(args.e2e_steps + 1):
-            name = names[i % len(names)]
-            h_w.copy_(weights[name])
-            torch.cuda.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            rc = wrs.table_build_host(table.handle, h_w.data_ptr(), n, wrs.F32, sh)
-            assert rc == wrs.OK, wrs.status_str(rc)
-            rc = wrs.sample_host(table.handle, k, 5000 + i, 0, h_out.data_ptr(), sh)
-            assert rc == wrs.OK, wrs.status_str(rc)
-            e1.record(stream)
-            e1.synchronize()
-            if i > 0:  # first call allocates the staging buffers
-                times.append(e0.elapsed_time(e1))
-        t_e2e = reduce_max([statistics.mean(times)], "cuda")[0]
-        e2e = {"value": ws * n / (t_e2e * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": 4 * n,
-               "d2h_bytes_per_step": 4 * k, "ms_per_step": t_e2e,
-               "note": "wrs_table_build_host (H2D of the weights) + wrs_sample_host (D2H of the samples)"}
+        e2e = run_e2e(args, torch, wrs, table, weights, names, stream, ws)
 
     psa_plus = None
     if not args.no_psa_plus:
