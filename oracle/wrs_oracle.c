@@ -662,6 +662,9 @@ static double det_u128_to_double(u128 x)
     return det_ldexp((double)(uint64_t)m, sh);
 }
 
+/* 1/k for k = 1..40, each the nearest binary64 (folded by the compiler)  */
+static const double DET_INV[41] = {0.0, 1.0 / 1.0, 1.0 / 2.0, 1.0 / 3.0, 1.0 / 4.0, 1.0 / 5.0, 1.0 / 6.0, 1.0 / 7.0, 1.0 / 8.0, 1.0 / 9.0, 1.0 / 10.0, 1.0 / 11.0, 1.0 / 12.0, 1.0 / 13.0, 1.0 / 14.0, 1.0 / 15.0, 1.0 / 16.0, 1.0 / 17.0, 1.0 / 18.0, 1.0 / 19.0, 1.0 / 20.0, 1.0 / 21.0, 1.0 / 22.0, 1.0 / 23.0, 1.0 / 24.0, 1.0 / 25.0, 1.0 / 26.0, 1.0 / 27.0, 1.0 / 28.0, 1.0 / 29.0, 1.0 / 30.0, 1.0 / 31.0, 1.0 / 32.0, 1.0 / 33.0, 1.0 / 34.0, 1.0 / 35.0, 1.0 / 36.0, 1.0 / 37.0, 1.0 / 38.0, 1.0 / 39.0, 1.0 / 40.0};
+
 /* natural logarithm of x > 0: x = f 2^e with f in [sqrt(1/2), sqrt(2)),   */
 /* log f = 2 atanh(s), s = (f - 1) / (f + 1), |s| < 0.172, series to s^25  */
 static double det_log(double x)
@@ -682,8 +685,8 @@ static double det_log(double x)
     if (f > 1.4142135623730951) { f = f * 0.5; e += 1; }
     s = (f - 1.0) / (f + 1.0);
     s2 = s * s;
-    acc = 1.0 / 25.0;
-    for (k = 11; k >= 0; --k) acc = acc * s2 + 1.0 / (double)(2 * k + 1);
+    acc = DET_INV[25];
+    for (k = 11; k >= 0; --k) acc = acc * s2 + DET_INV[2 * k + 1];
     return (double)e * 0.6931471805599453 + 2.0 * s * acc;
 }
 
@@ -694,12 +697,13 @@ static double det_log1m(double p)
     double acc;
     int k;
     if (p >= 0.25) return det_log(1.0 - p);
-    acc = 1.0 / 40.0;
-    for (k = 39; k >= 1; --k) acc = acc * p + 1.0 / (double)k;
+    acc = DET_INV[40];
+    for (k = 39; k >= 1; --k) acc = acc * p + DET_INV[k];
     return -p * acc;
 }
 
-/* e^x: x = k ln2 + r, |r| <= ln2 / 2 (+ rounding), Taylor to r^20 */
+/* e^x: x = k ln2 + r, |r| <= ln2 / 2 (+ rounding), Taylor to r^20 in     */
+/* Horner form, each term's 1/j a constant: acc = 1 + (r / j) acc           */
 static double det_exp(double x)
 {
     double kd, r, acc;
@@ -709,7 +713,7 @@ static double det_exp(double x)
     k = (int)kd;
     r = x - kd * 0.6931471805599453;
     acc = 1.0;
-    for (j = 20; j >= 1; --j) acc = acc * r / (double)j + 1.0;
+    for (j = 20; j >= 1; --j) acc = acc * (r * DET_INV[j]) + 1.0;
     return det_ldexp(acc, k);
 }
 
@@ -746,7 +750,8 @@ static double os_unif(os_rng *r)
     return (double)(w >> 11) * 0x1p-53;
 }
 
-/* log(k!) : exact product and det_log below 10, Stirling's series above */
+/* log(k!) : exact product and det_log below 10, Stirling's series above  */
+/* (with 1/(k+1) formed once)                                               */
 static double det_lfact(uint64_t k)
 {
     if (k < 10) {
@@ -755,8 +760,8 @@ static double det_lfact(uint64_t k)
         for (i = 2; i <= k; ++i) f *= (double)i;
         return det_log(f);
     } else {
-        double z = (double)k + 1.0, z2 = z * z;
-        double corr = (1.0 / 12.0 - (1.0 / 360.0 - (1.0 / 1260.0 - (1.0 / 1680.0) / z2) / z2) / z2) / z;
+        double z = (double)k + 1.0, iz = 1.0 / z, iz2 = iz * iz;
+        double corr = (1.0 / 12.0 - (1.0 / 360.0 - (1.0 / 1260.0 - (1.0 / 1680.0) * iz2) * iz2) * iz2) * iz;
         return ((double)k + 0.5) * det_log(z) - z + 0.5 * det_log(6.283185307179586) + corr;
     }
 }
@@ -781,7 +786,7 @@ static uint64_t os_binomial(uint64_t n, u128 num, u128 den, os_rng *rng)
                 u -= r;
                 x++;
                 if (x > n) break;
-                r *= a / (double)x - s;
+                r *= (x <= 40 ? a * DET_INV[x] : a / (double)x) - s;
             }
             if (x <= n) break;
             if (rng->j >= OS_MAX_DRAWS) { x = (uint64_t)((double)n * p); break; }

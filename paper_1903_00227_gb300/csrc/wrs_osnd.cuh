@@ -52,6 +52,9 @@ __device__ __forceinline__ double os_u128_to_double(u128 x)
     return os_ldexp((double)(uint64_t)m, sh);
 }
 
+// 1/k for k = 1..40, each the nearest binary64 (folded by the compiler)
+__device__ const double kOsInv[41] = {0.0, 1.0 / 1.0, 1.0 / 2.0, 1.0 / 3.0, 1.0 / 4.0, 1.0 / 5.0, 1.0 / 6.0, 1.0 / 7.0, 1.0 / 8.0, 1.0 / 9.0, 1.0 / 10.0, 1.0 / 11.0, 1.0 / 12.0, 1.0 / 13.0, 1.0 / 14.0, 1.0 / 15.0, 1.0 / 16.0, 1.0 / 17.0, 1.0 / 18.0, 1.0 / 19.0, 1.0 / 20.0, 1.0 / 21.0, 1.0 / 22.0, 1.0 / 23.0, 1.0 / 24.0, 1.0 / 25.0, 1.0 / 26.0, 1.0 / 27.0, 1.0 / 28.0, 1.0 / 29.0, 1.0 / 30.0, 1.0 / 31.0, 1.0 / 32.0, 1.0 / 33.0, 1.0 / 34.0, 1.0 / 35.0, 1.0 / 36.0, 1.0 / 37.0, 1.0 / 38.0, 1.0 / 39.0, 1.0 / 40.0};
+
 // natural logarithm of x > 0: x = f 2^e with f in [sqrt(1/2), sqrt(2)),
 // log f = 2 atanh(s), s = (f - 1) / (f + 1), series to s^25
 __device__ __forceinline__ double os_log(double x)
@@ -67,7 +70,8 @@ __device__ __forceinline__ double os_log(double x)
     if (f > 1.4142135623730951) { f = f * 0.5; e += 1; }
     const double s = (f - 1.0) / (f + 1.0), s2 = s * s;
     double acc = 1.0 / 25.0;
-    for (int k = 11; k >= 0; --k) acc = acc * s2 + 1.0 / (double)(2 * k + 1);
+#pragma unroll
+    for (int k = 11; k >= 0; --k) acc = acc * s2 + 1.0 / (double)(2 * k + 1); // constants once unrolled
     return (double)e * 0.6931471805599453 + 2.0 * s * acc;
 }
 
@@ -77,18 +81,21 @@ __device__ __forceinline__ double os_log1m(double p)
 {
     if (p >= 0.25) return os_log(1.0 - p);
     double acc = 1.0 / 40.0;
-    for (int k = 39; k >= 1; --k) acc = acc * p + 1.0 / (double)k;
+#pragma unroll
+    for (int k = 39; k >= 1; --k) acc = acc * p + 1.0 / (double)k; // constants once unrolled
     return -p * acc;
 }
 
-// e^x: x = k ln2 + r, Taylor series of e^r to r^20
+// e^x: x = k ln2 + r, Taylor series of e^r to r^20 in Horner form with each
+// term's 1/j a constant: acc = 1 + (r / j) acc
 __device__ __forceinline__ double os_exp(double x)
 {
     if (x < -745.0) return 0.0;
     const double kd = floor(x / 0.6931471805599453 + 0.5);
     const double r = x - kd * 0.6931471805599453;
     double acc = 1.0;
-    for (int j = 20; j >= 1; --j) acc = acc * r / (double)j + 1.0;
+#pragma unroll
+    for (int j = 20; j >= 1; --j) acc = acc * (r * (1.0 / (double)j)) + 1.0;
     return os_ldexp(acc, (int)kd);
 }
 
@@ -126,16 +133,17 @@ __device__ __forceinline__ double os_unif(OsRng &r)
 }
 
 // log(k!): exact product and os_log below 10, Stirling's series above
-__device__ __forceinline__ double os_lfact(uint64_t k)
+// (with 1/(k+1) formed once); hl2pi = 0.5 * os_log(2 pi), passed in
+__device__ __forceinline__ double os_lfact(uint64_t k, double hl2pi)
 {
     if (k < 10) {
         double f = 1.0;
         for (uint64_t i = 2; i <= k; ++i) f *= (double)i;
         return os_log(f);
     }
-    const double z = (double)k + 1.0, z2 = z * z;
-    const double corr = (1.0 / 12.0 - (1.0 / 360.0 - (1.0 / 1260.0 - (1.0 / 1680.0) / z2) / z2) / z2) / z;
-    return ((double)k + 0.5) * os_log(z) - z + 0.5 * os_log(6.283185307179586) + corr;
+    const double z = (double)k + 1.0, iz = 1.0 / z, iz2 = iz * iz;
+    const double corr = (1.0 / 12.0 - (1.0 / 360.0 - (1.0 / 1260.0 - (1.0 / 1680.0) * iz2) * iz2) * iz2) * iz;
+    return ((double)k + 0.5) * os_log(z) - z + hl2pi + corr;
 }
 
 // Binomial(n, num / den), 0 < num < den
@@ -154,7 +162,7 @@ __device__ uint64_t os_binomial(uint64_t n, u128 num, u128 den, OsRng &rng)
                 u -= r;
                 x++;
                 if (x > n) break;
-                r *= a / (double)x - s;
+                r *= (x <= 40 ? a * kOsInv[x] : a / (double)x) - s;
             }
             if (x <= n) break;
             if (rng.j >= kOsMaxDraws) { x = (uint64_t)((double)n * p); break; }
@@ -162,9 +170,12 @@ __device__ uint64_t os_binomial(uint64_t n, u128 num, u128 den, OsRng &rng)
     } else { // BTRS
         const double spq = sqrt((double)n * p * q);
         const double b = 1.15 + 2.53 * spq, a = -0.0873 + 0.0248 * b + 0.01 * p, c = (double)n * p + 0.5;
-        const double vr = 0.92 - 4.2 / b, alpha = (2.83 + 5.1 / b) * spq, lpq = os_log(p / q);
+        const double vr = 0.92 - 4.2 / b, alpha = (2.83 + 5.1 / b) * spq;
         const uint64_t m = (uint64_t)floor(((double)n + 1.0) * p);
-        const double h = os_lfact(m) + os_lfact(n - m);
+        // log(p/q), log(m!) + log((n-m)!) and 0.5 log(2 pi) are needed only when
+        // the quick acceptance test fails: formed then, once (same values)
+        double lpq = 0.0, h = 0.0, hl2pi = 0.0;
+        bool slow = false;
         for (;;) {
             const double u = os_unif(rng) - 0.5;
             double v = os_unif(rng);
@@ -174,8 +185,14 @@ __device__ uint64_t os_binomial(uint64_t n, u128 num, u128 den, OsRng &rng)
             if (kd < 0.0 || kd > (double)n) continue;
             x = (uint64_t)kd;
             if (us >= 0.07 && v <= vr) break;
+            if (!slow) {
+                hl2pi = 0.5 * os_log(6.283185307179586);
+                lpq = os_log(p / q);
+                h = os_lfact(m, hl2pi) + os_lfact(n - m, hl2pi);
+                slow = true;
+            }
             v = os_log(v * alpha / (a / (us * us) + b));
-            if (v <= h - os_lfact(x) - os_lfact(n - x) + ((double)x - (double)m) * lpq) break;
+            if (v <= h - os_lfact(x, hl2pi) - os_lfact(n - x, hl2pi) + ((double)x - (double)m) * lpq) break;
         }
     }
     return flip ? n - x : x;
