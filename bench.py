@@ -233,12 +233,53 @@ def cpu_oracle_run(names, n_s: int, repeats: int = 1):
     return tb, ts, nw, nsmp, steps
 
 
+def cpu_other_builders(names, n_s: int):
+    """The oracle's other sequential builders on the same bounded sample, as
+    they stand (one thread): Vose's method in binary64 (Alg. 1, the paper's
+    sequential baseline) and the exact PSA (Alg. 3) with 64 subproblems run
+    one after another."""
+    from oracle import wrs_oracle as O
+    from paper_1903_00227_gb300 import workloads as WL
+
+    tv = tp = 0.0
+    nw = 0
+    for name in names:
+        kind, s, seed = DISTS[name]
+        w = WL.generate(kind, n_s, seed, s)
+        t0 = time.perf_counter()
+        O.vose_f64(w)
+        t1 = time.perf_counter()
+        O.psa(O.quantize(w), 64)
+        t2 = time.perf_counter()
+        tv += t1 - t0
+        tp += t2 - t1
+        nw += n_s
+    return {"vose_f64_gweights_s": nw / tv / 1e9, "psa64_gweights_s": nw / tp / 1e9}
+
+
 def cpu_baseline(names, n_s: int):
     tb, ts, nw, nsmp, _ = cpu_oracle_run(names, n_s)
-    return {"value": nw / tb / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample_gsamples_s": nsmp / ts / 1e9,
-            "sample": f"first {n_s:,} weights of each of {', '.join(names)} (same recipes), "
-                      f"exact quantize + Alg. 2 sweep, then {n_s:,} queries each; single thread"}
+    out = {"value": nw / tb / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample_gsamples_s": nsmp / ts / 1e9,
+           "sample": f"first {n_s:,} weights of each of {', '.join(names)} (same recipes), "
+                     f"exact quantize + Alg. 2 sweep, then {n_s:,} queries each; single thread"}
+    out.update(cpu_other_builders(names, n_s))
+    out["cpu_model"] = cpu_model()
+    out["host_threads"] = os.cpu_count()
+    return out
+
+
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+
+    return platform.machine()
 
 
 def config(args, names):
