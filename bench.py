@@ -590,6 +590,21 @@ def run_e2e(args, torch, wrs, table, weights, names, stream, ws):
         h_in[name].copy_(weights[name])
     h_out = [torch.empty(k, dtype=torch.int32, pin_memory=True) for _ in range(2)]
     torch.cuda.synchronize()
+    # the host link's own rate on this machine (1 GB each way, best of 3), for context
+    link = {"h2d": 0.0, "d2h": 0.0}
+    nl = min(k, 250_000_000)
+    dbuf = torch.empty(nl, dtype=torch.int32, device="cuda")
+    for _ in range(3):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        dbuf.copy_(h_out[0][:nl], non_blocking=True)
+        e1.record(stream)
+        h_out[1][:nl].copy_(dbuf, non_blocking=True)
+        e2.record(stream)
+        e2.synchronize()
+        link["h2d"] = max(link["h2d"], 4 * nl / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+        link["d2h"] = max(link["d2h"], 4 * nl / (e1.elapsed_time(e2) * 1e-3) / 1e9)
+    del dbuf
 
     def build_host(t, name, sh):
         rc = wrs.table_build_host(t.handle, h_in[name].data_ptr(), n, wrs.F32, sh)
@@ -648,6 +663,7 @@ def run_e2e(args, torch, wrs, table, weights, names, stream, ws):
     return {"value": ws * n / (t_pipe * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": 4 * n,
             "d2h_bytes_per_step": 4 * k, "ms_per_step": t_pipe, "steps": steps,
             "serial": {"value": ws * n / (t_serial * 1e-3) / 1e9, "ms_per_step": t_serial},
+            "host_link_gbs": link,
             "note": "wrs_table_build_host (H2D of the weights) + wrs_sample_host (D2H of the samples) per step; "
                     "two table objects and two streams, step i+1's upload and build issued before step i's "
                     "sampling; serial = one table, one step at a time"}
