@@ -49,6 +49,7 @@ DISTS = {  # name -> (generator kind, Zipf exponent, seed)
 # algorithmic bytes per unit (weights for the build kernels, samples for the query)
 ALGO_BYTES = {"stats": 4, "stats_combine": 0, "classify": 4, "tilescan": 0, "split": 0, "sweep": 16, "sample": 16}
 BUILD_BYTES_PER_WEIGHT = 24  # three 4-B weight reads + 12-B (threshold, alias) payload
+SECTOR_BYTES_PER_SAMPLE = 36  # a random gather's floor: one 32-B sector + a 4-B coalesced store
 KERNEL_NAMES = {"stats": "k_stats", "stats_combine": "k_stats_combine", "classify": "k_classify",
                 "tilescan": "k_tilescan", "split": "k_split", "sweep": "k_sweep", "sample": "k_sample"}
 
@@ -821,7 +822,10 @@ def run_ours(args, names):
             "ms_per_step": statistics.mean(step_ms), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u128", "data": "synthetic", "config": config(args, names),
             "sample": {"value": sample_rate, "unit": "Gsamples/s", "ms": t_sample / K,
-                       "random_gather_ceiling": gather},
+                       "random_gather_ceiling": gather,
+                       "sector_roofline": {"bytes_per_sample": SECTOR_BYTES_PER_SAMPLE,
+                                           "frac": sample_rate * SECTOR_BYTES_PER_SAMPLE / peak,
+                                           "note": "one 32-B sector per random bucket + a 4-B coalesced store"}},
             "p99_ms": p99,
             "roofline": roofline,
             "roofline_build": {"bound": "hbm", "achieved": ach_build, "peak": peak, "unit": "GB/s",

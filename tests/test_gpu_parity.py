@@ -189,3 +189,43 @@ def test_host_buffer_entry_points():
         out = np.zeros(50_000, np.uint32)
         assert wrs.sample_host(t.handle, 50_000, 9, 1, out.ctypes.data, 0) == wrs.OK
     assert np.array_equal(out, O.sample(tab.thr, tab.alias, tab.Qp, 50_000, 9, 1))
+
+
+def test_host_entry_points_double_buffered():
+    """The end-to-end schedule the benchmark times: two table objects on two
+    CUDA streams, step i+1's wrs_table_build_host issued before step i's
+    wrs_sample_host, so an upload and a build overlap the other table's
+    sampling.  Every step's samples equal the oracle's for its weights."""
+    n, k = 3 * TILE + 11, 40_000
+    inputs = [WL.f32_zipf(n, 1.0, 21), WL.f32_uniform(n, 22), WL.u32_uniform(n, 23).view(np.float32),
+              WL.f32_zipf(n, 1.5, 24)]
+    dtypes = [wrs.F32, wrs.F32, wrs.U32, wrs.F32]
+    want = []
+    for i, (w, dt) in enumerate(zip(inputs, dtypes)):
+        qz, tab = O.build_table(w.view(np.uint32) if dt == wrs.U32 else w)
+        want.append(O.sample(tab.thr, tab.alias, tab.Qp, k, 300 + i, 0))
+    h_in = [torch.from_numpy(np.ascontiguousarray(w)).pin_memory() for w in inputs]
+    h_out = [torch.empty(k, dtype=torch.int32).pin_memory() for _ in range(2)]
+    tables = [wrs.AliasTable(n), wrs.AliasTable(n)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    try:
+        def build(i):
+            t = i % 2
+            assert wrs.table_build_host(tables[t].handle, h_in[i].data_ptr(), n, dtypes[i],
+                                        streams[t].cuda_stream) == wrs.OK
+            tables[t].n = n
+
+        build(0)
+        for i in range(len(inputs)):
+            if i + 1 < len(inputs):
+                build(i + 1)
+            t = i % 2
+            assert wrs.sample_host(tables[t].handle, k, 300 + i, 0, h_out[t].data_ptr(),
+                                   streams[t].cuda_stream) == wrs.OK
+            got = h_out[t].numpy().view(np.uint32).copy()
+            assert np.array_equal(got, want[i]), i
+        torch.cuda.synchronize()
+        assert all(t.status() == wrs.OK for t in tables)
+    finally:
+        for t in tables:
+            t.free()
