@@ -258,6 +258,63 @@ def cpu_other_builders(names, n_s: int):
     return {"vose_f64_gweights_s": nw / tv / 1e9, "psa64_gweights_s": nw / tp / 1e9}
 
 
+def cpu_rows(names, n_s: int, batch_tables: int):
+    """The oracle timed beside each of the other rows, one thread, on bounded
+    samples of the same recipes (quantisation included in every build)."""
+    from oracle import wrs_oracle as O
+    from paper_1903_00227_gb300 import workloads as WL
+
+    res = {}
+    tq = tpp = t2b = t2s = 0.0
+    nw = 0
+    tl_z = qz_z = None
+    for name in names:
+        kind, s, seed = DISTS[name]
+        w = WL.generate(kind, n_s, seed, s)
+        t0 = time.perf_counter()
+        qz = O.quantize(w)
+        t1 = time.perf_counter()
+        O.psa_plus(qz, 2048)
+        t2 = time.perf_counter()
+        tl = O.build_2lvl(qz)
+        t3 = time.perf_counter()
+        O.sample_2lvl(tl, n_s, 3, 0)
+        t4 = time.perf_counter()
+        tq += t1 - t0
+        tpp += t2 - t1
+        t2b += t3 - t2
+        t2s += t4 - t3
+        nw += n_s
+        if name == "zipf1.5":
+            tl_z, qz_z = tl, qz
+    sample = f"first {n_s:,} weights of each of {', '.join(names)}; one thread"
+    res["psa_plus"] = {"build_gweights_s": nw / (tq + tpp) / 1e9, "cores": 1, "sample": sample}
+    res["two_level"] = {"build_gweights_s": nw / (tq + t2b) / 1e9, "sample_gsamples_s": nw / t2s / 1e9,
+                        "cores": 1, "sample": sample}
+    if tl_z is not None:
+        k = 10 ** 9
+        t0 = time.perf_counter()
+        items, _ = O.os_nd(qz_z, tl_z, k, 5, 0)
+        dt = time.perf_counter() - t0
+        res["os_nd"] = {"gsamples_s": k / dt / 1e9, "pairs": int(len(items)), "seconds": dt, "cores": 1,
+                        "sample": f"first {n_s:,} weights of zipf1.5, k = 10^9; one thread"}
+    if batch_tables > 0:
+        nb, kb, kinds, seeds = WL.batch_plan(batch_tables, 4)
+        m = min(256, len(nb))
+        ws_ = [WL.generate(kinds[t], nb[t], seeds[t], 1.0) for t in range(m)]
+        t0 = time.perf_counter()
+        for t in range(m):
+            qz = O.quantize(ws_[t])
+            tab = O.sweep(qz)
+            if kb[t]:
+                O.sample(tab.thr, tab.alias, tab.Qp, kb[t], 11, t)
+        dt = time.perf_counter() - t0
+        res["many_tables"] = {"gweights_s": sum(nb[:m]) / dt / 1e9, "tables_per_s": m / dt, "cores": 1,
+                              "sample": f"first {m} tables of the workload, quantize + Alg. 2 sweep + "
+                                        "their samples; one thread"}
+    return res
+
+
 def cpu_baseline(names, n_s: int):
     tb, ts, nw, nsmp, _ = cpu_oracle_run(names, n_s)
     out = {"value": nw / tb / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -813,6 +870,12 @@ def run_ours(args, names):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(names, min(args.cpu_sample, n))
+        rows = cpu_rows(names, min(args.cpu_sample // 4, n), args.batch_tables)
+        for key, row in (("psa_plus", psa_plus), ("two_level", two_level), ("many_tables", batched)):
+            if row is not None and key in rows:
+                row["cpu_oracle"] = rows[key]
+        if two_level is not None and two_level.get("os_nd") is not None and "os_nd" in rows:
+            two_level["os_nd"]["cpu_oracle"] = rows["os_nd"]
 
     if rank == 0:
         srt = sorted(step_ms)
