@@ -813,6 +813,7 @@ __device__ __forceinline__ void sweep_body(const uint32_t *__restrict__ w, uint6
     const uint32_t light_max = hdr->light_max;
     const int beta = hdr->beta;
     const uint32_t shift = hdr->shift;
+    const bool narrow = shift == 0; // Q < 2^64, the same for the whole grid
     bool bad = false;
 
     uint32_t x[kItems], y[kItems];
@@ -921,6 +922,34 @@ __device__ __forceinline__ void sweep_body(const uint32_t *__restrict__ w, uint6
                 u128 di = i < nl ? S.okey[swz(i)] : D_end; // key of light i (D_end past the last)
                 for (uint32_t st = 0; st < steps; ++st) {
                     const bool heavy_next = (j < b1) && (i >= a1 || ej <= di);
+                    if (narrow) {
+                        // Q < 2^64 (shift 0): a bucket's mass, a light's deficit
+                        // and a heavy's gap D - E (< Q when the build is sound,
+                        // checked in full) are 64-bit; only the keys are wider
+                        const uint64_t Q64 = lo64(Q);
+                        if (heavy_next) {
+                            const u128 gap = di - ej;
+                            if (hi64(gap) != 0 || lo64(gap) >= Q64) bad = true;
+                            const uint64_t bw = Q64 - lo64(gap);
+                            const uint32_t me = (uint32_t)(sbase + S.hoff[j]);
+                            const uint32_t nx = (j + 1 < hc) ? (uint32_t)(sbase + S.hoff[j + 1]) : split[s].next_heavy;
+                            if (nx == kNone && bw != Q64) bad = true;
+                            const uint32_t alias = (nx == kNone || bw == Q64) ? me : nx;
+                            table[me] = make_uint4((uint32_t)bw, (uint32_t)(bw >> 32), alias, 0u);
+                            ++j;
+                            if (j < b1) ej = S.hkey[swz(j)];
+                        } else {
+                            const u128 dn = (i + 1 < nl) ? S.okey[swz(i + 1)] : D_end;
+                            const uint64_t def = lo64(dn) - lo64(di); // < Q: exact modulo 2^64
+                            const uint64_t nq = Q64 - def;
+                            const uint32_t me = (uint32_t)(tile0 + S.ooff[i]);
+                            const uint32_t alias = (def == 0) ? me : (uint32_t)(sbase + S.hoff[j]);
+                            table[me] = make_uint4((uint32_t)nq, (uint32_t)(nq >> 32), alias, 0u);
+                            ++i;
+                            di = dn;
+                        }
+                        continue;
+                    }
                     if (heavy_next) {
                         const u128 gap = di - ej;
                         if (gap >= Q) bad = true;
