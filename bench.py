@@ -674,19 +674,21 @@ def run_e2e(args, torch, wrs, table, weights, names, stream, ws):
 
     # serial: one table, one step at a time (first call allocates the staging buffers)
     sh0 = stream.cuda_stream
-    times = []
+    times, t_up, t_down = [], [], []
     for i in range(K + 1):
         name = names[i % len(names)]
         torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
+        e0, em, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)
         build_host(table, name, sh0)
+        em.record(stream)
         sample_host(table, i, 0, sh0)
         e1.record(stream)
         e1.synchronize()
         if i > 0:
             times.append(e0.elapsed_time(e1))
+            t_up.append(e0.elapsed_time(em))
+            t_down.append(em.elapsed_time(e1))
     t_serial = reduce_max([statistics.mean(times)], "cuda")[0]
 
     # pipelined: two table objects on two streams
@@ -720,7 +722,8 @@ def run_e2e(args, torch, wrs, table, weights, names, stream, ws):
     del h_in, h_out
     return {"value": ws * n / (t_pipe * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": 4 * n,
             "d2h_bytes_per_step": 4 * k, "ms_per_step": t_pipe, "steps": steps,
-            "serial": {"value": ws * n / (t_serial * 1e-3) / 1e9, "ms_per_step": t_serial},
+            "serial": {"value": ws * n / (t_serial * 1e-3) / 1e9, "ms_per_step": t_serial,
+                       "upload_build_ms": statistics.mean(t_up), "sample_download_ms": statistics.mean(t_down)},
             "host_link_gbs": link,
             "note": "wrs_table_build_host (H2D of the weights) + wrs_sample_host (D2H of the samples) per step; "
                     "two table objects and two streams, step i+1's upload and build issued before step i's "
