@@ -648,21 +648,25 @@ def run_e2e(args, torch, wrs, table, weights, names, stream, ws):
         h_in[name].copy_(weights[name])
     h_out = [torch.empty(k, dtype=torch.int32, pin_memory=True) for _ in range(2)]
     torch.cuda.synchronize()
-    # the host link's own rate on this machine (1 GB each way, best of 3), for context
-    link = {"h2d": 0.0, "d2h": 0.0}
-    nl = min(k, 250_000_000)
-    dbuf = torch.empty(nl, dtype=torch.int32, device="cuda")
-    for _ in range(3):
-        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-        e0.record(stream)
-        dbuf.copy_(h_out[0][:nl], non_blocking=True)
-        e1.record(stream)
-        h_out[1][:nl].copy_(dbuf, non_blocking=True)
-        e2.record(stream)
-        e2.synchronize()
-        link["h2d"] = max(link["h2d"], 4 * nl / (e0.elapsed_time(e1) * 1e-3) / 1e9)
-        link["d2h"] = max(link["d2h"], 4 * nl / (e1.elapsed_time(e2) * 1e-3) / 1e9)
+    # the host link's rate on this machine for each pinned buffer the step uses
+    # (whole buffer, best of 2), for context: the upload reads h_in, the
+    # download writes h_out
+    def copy_rate(dst, src, nbytes):
+        best = 0.0
+        for _ in range(2):
+            e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+            e0.record(stream)
+            dst.copy_(src, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            best = max(best, nbytes / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+        return best
+
+    dbuf = torch.empty(max(n, k), dtype=torch.int32, device="cuda")
+    up = {name: copy_rate(dbuf[:n].view(torch.float32), h_in[name], 4 * n) for name in names}
+    down = [copy_rate(h, dbuf[:k], 4 * k) for h in h_out]
     del dbuf
+    link = {"h2d": min(up.values()), "d2h": min(down), "h2d_per_input": up, "d2h_per_output": down}
 
     def build_host(t, name, sh):
         rc = wrs.table_build_host(t.handle, h_in[name].data_ptr(), n, wrs.F32, sh)
