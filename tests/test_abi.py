@@ -72,3 +72,47 @@ def test_batch_offsets_host_only(wrs):
     assert wrs.batch_sample(None, 1, 0, 0, 0) == wrs.EINVAL
     assert wrs.batch_buckets(None) == 0
     wrs.batch_free(None)
+
+
+def test_every_entry_point_rejects_null_handles_without_a_gpu(wrs):
+    """Null handles and missing buffers are refused with WRS_EINVAL before any
+    CUDA call, for every entry point that takes a table, a batch or a task
+    list (the library is loaded on a machine with no GPU)."""
+    lib = wrs._lib  # argument and result types as the binding declares them
+    E = wrs.EINVAL
+    # single tables
+    assert wrs.table_build_host(None, 0, 10, wrs.F32, 0) == E
+    assert wrs.sample_host(None, 10, 1, 0, 0, 0) == E
+    assert wrs.table_upload(None, 0, 10, 1, 0, 0) == E
+    assert wrs.table_set_timing(None, True) == E
+    assert wrs.table_build_psa_plus(None, 0, 10, wrs.F32, 0) == E
+    assert wrs.table_psa_plus_leftovers(None)[0] == E
+    assert lib.wrs_table_info_get(None, None) == E
+    assert lib.wrs_table_device_header(None) is None
+    # the allocation-free build: missing buffers, sizes past its scratch
+    assert wrs.build_noalloc(0, 10, wrs.F32, 0, 0, 0) == E
+    assert wrs.build_noalloc(16, 0, wrs.F32, 16, 16, 0) == E
+    # batches
+    assert lib.wrs_batch_create(0, None, None) == E
+    assert wrs.batch_build(None, 16, wrs.F32, 0) == E
+    assert wrs.batch_sample(None, 1, 0, 16, 0) == E
+    assert wrs.batch_download(None, 16, 16) == E
+    assert lib.wrs_batch_layout(None, None) == E
+    assert lib.wrs_batch_groups(None, None) == E
+    assert lib.wrs_batch_set_groups(None, None) == E
+    assert lib.wrs_batch_status(None, None) == E
+    assert lib.wrs_batch_buckets(None) is None
+    assert lib.wrs_batch_device_header(None, 0) is None
+    wrs.batch_free(None)
+    # many sample requests: nothing to draw is fine, a missing task list is not
+    assert wrs.sample_many(0, 0, 0, 0, 0) == wrs.OK
+    assert wrs.sample_many(0, 1, 10, 16, 0) == E
+    assert wrs.sample_many(8, 1, 10, 16, 0) == E  # task list not 16-byte aligned
+    # two-level tables and OS-ND
+    assert wrs.table2_build(None, 16, 10, wrs.F32, 0) == E
+    assert wrs.table2_sample(None, 10, 1, 0, 16, 0) == E
+    assert wrs.table2_status(None) == E
+    assert wrs.table2_download(None, 16, 16, 16, 16) == E
+    assert lib.wrs_table2_layout(None, None, None) == E
+    assert lib.wrs_table2_sample_os(None, None, 1, 10, 1, 0, None, None, 0, None, None) == E
+    wrs.table2_free(None)
