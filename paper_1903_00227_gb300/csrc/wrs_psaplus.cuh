@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_pp_local(const uint32_t *__rest
 // bsum[b] = the block's total); k_pp_scan2 (one block) turns bsum into
 // exclusive block prefixes and writes the grand total to tot.  n < 2^32
 // gives at most 2^21 tiles, so at most 1024 blocks.
-__device__ __forceinline__ void pp_scan_block(TileSum (&v)[kItems], uint32_t count, TileSum &total)
+__device__ __forceinline__ void pp_scan_block(TileSum (&v)[kItems], TileSum &total)
 {
     __shared__ U2 s_scan[kWarps];
     __shared__ uint32_t s_c1[kWarps], s_c2[kWarps];
@@ -282,7 +282,6 @@ __device__ __forceinline__ void pp_scan_block(TileSum (&v)[kItems], uint32_t cou
     }
     total.l_lo = lo64(tot.a); total.l_hi = hi64(tot.a); total.h_lo = lo64(tot.b); total.h_hi = hi64(tot.b);
     total.cl = t1; total.nheavy = t2; total.first_heavy = kNone; total.pad = 0;
-    (void)count;
 }
 
 __global__ void __launch_bounds__(kThreads) k_pp_scan1(const TileSum *__restrict__ tsum, uint32_t ntiles,
@@ -295,7 +294,7 @@ __global__ void __launch_bounds__(kThreads) k_pp_scan1(const TileSum *__restrict
 #pragma unroll
     for (int k = 0; k < kItems; ++k) v[k] = t0 + k < ntiles ? tilesum_ldcg(tsum + t0 + k) : pp_zero();
     TileSum total;
-    pp_scan_block(v, ntiles, total);
+    pp_scan_block(v, total);
 #pragma unroll
     for (int k = 0; k < kItems; ++k)
         if (t0 + k < ntiles) tilesum_st(tpre + t0 + k, v[k]);
@@ -311,7 +310,7 @@ __global__ void __launch_bounds__(kThreads) k_pp_scan2(TileSum *bsum, uint32_t n
 #pragma unroll
     for (int k = 0; k < kItems; ++k) v[k] = b0 + k < nblocks ? tilesum_ldcg(bsum + b0 + k) : pp_zero();
     TileSum total;
-    pp_scan_block(v, nblocks, total);
+    pp_scan_block(v, total);
 #pragma unroll
     for (int k = 0; k < kItems; ++k)
         if (b0 + k < nblocks) tilesum_st(bsum + b0 + k, v[k]);
