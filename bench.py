@@ -315,6 +315,29 @@ def cpu_rows(names, n_s: int, batch_tables: int):
     return res
 
 
+def cpu_sample_all_cores(n_s: int):
+    """The oracle's sampler on every host core: threads draw disjoint ranges
+    of sample indices with the oracle's indexed query (ctypes releases the
+    interpreter lock during the C call), from a table of n_s uniform weights."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import numpy as np
+
+    from oracle import wrs_oracle as O
+    from paper_1903_00227_gb300 import workloads as WL
+
+    kind, s, seed = DISTS["uniform"]
+    qz, tab = O.build_table(WL.generate(kind, n_s, seed, s))
+    nt = max(1, os.cpu_count() or 1)
+    k = 4 * n_s
+    chunks = [np.arange(i * k // nt, (i + 1) * k // nt, dtype=np.uint64) for i in range(nt)]
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(nt) as ex:
+        list(ex.map(lambda c: O.sample_at(tab.thr, tab.alias, tab.Qp, 2, 0, c), chunks))
+    dt = time.perf_counter() - t0
+    return {"sample_gsamples_s_all_cores": k / dt / 1e9, "sample_threads": nt}
+
+
 def cpu_baseline(names, n_s: int):
     tb, ts, nw, nsmp, _ = cpu_oracle_run(names, n_s)
     out = {"value": nw / tb / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -322,6 +345,7 @@ def cpu_baseline(names, n_s: int):
            "sample": f"first {n_s:,} weights of each of {', '.join(names)} (same recipes), "
                      f"exact quantize + Alg. 2 sweep, then {n_s:,} queries each; single thread"}
     out.update(cpu_other_builders(names, n_s))
+    out.update(cpu_sample_all_cores(n_s))
     out["cpu_model"] = cpu_model()
     out["host_threads"] = os.cpu_count()
     return out
