@@ -325,6 +325,24 @@ __device__ __forceinline__ TileSum tilesum_ldcg(const TileSum *p)
     return r;
 }
 
+// Sum of a u128 over the warp, returned to every lane: the warp-wide
+// reduction instruction adds 16-bit limbs exactly (each limb's sum over 32
+// lanes is below 2^21); the high half is skipped when every lane's is zero.
+__device__ __forceinline__ u128 warp_sum128(u128 v)
+{
+    const uint64_t lo = lo64(v), hi = hi64(v);
+    u128 r = 0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        r += (u128)__reduce_add_sync(0xFFFFFFFFu, (uint32_t)(lo >> (16 * c)) & 0xFFFFu) << (16 * c);
+    if (__any_sync(0xFFFFFFFFu, hi != 0)) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            r += (u128)__reduce_add_sync(0xFFFFFFFFu, (uint32_t)(hi >> (16 * c)) & 0xFFFFu) << (64 + 16 * c);
+    }
+    return r;
+}
+
 // Tiles t_first, t_first + t_stride, ... of one table.
 template <int F32>
 __device__ __forceinline__ void classify_body(const uint32_t *__restrict__ w, uint64_t n, int vec,
@@ -384,14 +402,10 @@ __device__ __forceinline__ void classify_body(const uint32_t *__restrict__ w, ui
         const uint32_t tn = t + t_stride;
         if (tn < ntiles) load_items(w, n, vec, (uint64_t)tn * kTile + (uint64_t)threadIdx.x * kItems, x);
         // block reduction of (L, H, counts, first heavy)
-        uint32_t cc = cl | (nh << 16), f = fh;
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) {
-            L += shfl_down128(L, d);
-            H += shfl_down128(H, d);
-            cc += __shfl_down_sync(0xFFFFFFFFu, cc, d);
-            f = min(f, __shfl_down_sync(0xFFFFFFFFu, f, d));
-        }
+        const uint32_t cc = __reduce_add_sync(0xFFFFFFFFu, cl | (nh << 16)); // <= 256 per field
+        const uint32_t f = __reduce_min_sync(0xFFFFFFFFu, fh);
+        L = warp_sum128(L);
+        H = warp_sum128(H);
         if (lane == 0) { s_l[wid] = L; s_h[wid] = H; s_c[wid] = cc; s_first[wid] = f; }
         __syncthreads();
         uint32_t ctot = 0;
