@@ -59,8 +59,7 @@ struct GroupSmem {
 __device__ __forceinline__ u128 block_sum128(u128 v, u128 *sm)
 {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) v += shfl_down128(v, d);
+    v = warp_sum128(v);
     if (lane == 0) sm[wid] = v;
     __syncthreads();
     u128 t = 0;
