@@ -159,3 +159,67 @@ def test_full_size_two_level():
     want = O.sample_2lvl_at(walk, 99, 3, pick.cpu().numpy().astype(np.uint64))
     assert np.array_equal(got, want)
     t2.free()
+
+
+def test_full_size_zipf15_shifted_coin():
+    """n = 10^9 binary32 Zipf 1.5 weights (the bench's third input): Q is near
+    2^69, so thresholds are shifted (thr = bw >> s, s > 0) and the build runs
+    on its 128-bit path.  Checked: the header against Python's exact sum;
+    10^6 sampled light buckets hold (n q) >> s exactly; every bucket's alias
+    is a heavy item or itself, full buckets point to themselves; and 10^5 of
+    10^9 samples equal the oracle's queries of the downloaded table."""
+    w = WL.generate_device("f32_zipf", N, 6, 1.5)
+    table = wrs.AliasTable(N)
+    table.build(w)
+    assert table.status() == wrs.OK
+    info = table.info()
+    assert info.shift > 0
+    host = np.empty(2 * N, dtype=np.uint64)
+    assert wrs.table_download(table.handle, host.ctypes.data, host.nbytes) == wrs.OK
+    thr_h = np.ascontiguousarray(host.reshape(N, 2)[:, 0])
+    word1 = host.reshape(N, 2)[:, 1]
+    alias_h = (word1 & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+    assert not (word1 >> np.uint64(32)).any()
+    del host, word1
+    bits = w.view(torch.int32).cpu().numpy().view(np.uint32)
+    light = bits <= np.uint32(info.light_max)
+    assert int(light.sum()) == info.n_light
+    # light buckets: exact n*q >> s on a sample, with Python integers
+    rng = np.random.default_rng(3)
+    lights = np.nonzero(light)[0]
+    pick = rng.choice(lights, 1_000_000, replace=False)
+    for i in pick[:20_000].tolist():  # Python big ints: the slow, obviously exact form
+        x = int(bits[i])
+        ex, m = (x >> 23) & 0xFF, x & 0x7FFFFF
+        if ex:
+            m |= 1 << 23
+        e = (ex if ex else 1) - 150 - info.beta
+        q = m << e if e >= 0 else m >> -e
+        assert int(thr_h[i]) == (N * q) >> info.shift, i
+    # the whole sample: q as exact integers (a light's q is below Q / n), then
+    # (N * q) >> s in Python integers
+    xs = bits[pick].astype(np.int64)
+    ex = (xs >> 23) & 0xFF
+    m = (xs & 0x7FFFFF) | (np.where(ex > 0, 1, 0) << 23)
+    e = np.where(ex > 0, ex, 1) - 150 - info.beta
+    assert e.max() <= 30
+    q = np.where(e >= 0, m << np.maximum(e, 0), m >> np.maximum(-e, 0)).astype(object)
+    got = thr_h[pick].astype(object)
+    want = (q * N) >> info.shift
+    assert (got == want).all()
+    # aliases: a heavy item or the bucket itself; full buckets point to themselves
+    idx = np.arange(N, dtype=np.uint32)
+    other = alias_h != idx
+    assert (~light[alias_h[other]]).all()
+    full = thr_h == np.uint64(info.qp)
+    assert (alias_h[full] == idx[full]).all()
+    assert (thr_h[other] < np.uint64(info.qp)).all()
+    del idx, other, full, light, bits, xs, m, e, q
+    # 10^9 samples; 10^5 of them recomputed by the oracle
+    k = 10 ** 9
+    out = table.sample(k, seed=77, stream_id=1)
+    sel = torch.randint(0, k, (100_000,), device="cuda", generator=torch.Generator(device="cuda").manual_seed(9))
+    got_s = out[sel].cpu().numpy().view(np.uint32)
+    want_s = O.sample_at(thr_h, alias_h, info.qp, 77, 1, sel.cpu().numpy().astype(np.uint64))
+    assert np.array_equal(got_s, want_s)
+    table.free()
