@@ -10,12 +10,19 @@ seeds.  Inputs (4 GB) exceed the 129 MB L2, so no flush is needed between
 steps.
 
 Printed JSON line (rank 0): ``value`` is the build throughput over all ranks
-in Gweights/s; ``sample`` gives the sampling throughput; ``e2e`` repeats the
+in Gweights/s; ``sample`` gives the sampling throughput (with a bare random
+gather's rate and the sector-limited roofline beside it); ``e2e`` repeats the
 step through the C ABI's host-buffer entry points with the host<->device
 copies inside the timed region (two table objects double-buffered; the
-serial one-table figure beside it); ``roofline`` is the dominant kernel against
-the measured HBM copy bandwidth; ``cpu_baseline`` times the CPU oracle on a
-bounded sample of the same workload.
+serial one-table figure, its phases and the host link's rate per buffer
+beside it); ``roofline`` is the dominant kernel against the measured HBM
+copy bandwidth, with its DRAM traffic from the committed ncu summaries;
+``cpu_baseline`` times the CPU oracle on a bounded sample of the same
+workload.  The other rows ride on the same line: ``psa_plus`` (PSA+ builds),
+``two_level`` (two-level tables, with ``os_nd`` output-sensitive sampling),
+``many_tables`` (4096 tables built and sampled in one CUDA graph against one
+table at a time) and ``serving`` (a Poisson request stream against one
+request at a time), each with the oracle timed beside it where it applies.
 
 ``--impl reference`` times the CPU oracle itself (the reference arm of this
 repository) on bounded samples of the same workload.
