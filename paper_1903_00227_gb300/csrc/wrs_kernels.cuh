@@ -810,7 +810,7 @@ __device__ __forceinline__ void load_heavies(SweepSmem &S, uint32_t t, const uin
     __syncthreads();
 }
 
-constexpr int kSweepTiles = 4; // own tiles per block of k_sweep (they share stream tiles)
+constexpr int kSweepTiles = 8; // own tiles per block of k_sweep (they share stream tiles)
 
 // Own tiles [c_first, c_last) of one table.
 template <int F32>
