@@ -932,6 +932,7 @@ uint64_t wo_binomial(uint64_t n, uint64_t num, uint64_t den, uint64_t seed, uint
 
 double wo_det_log(double x) { return det_log(x); }
 double wo_det_log1m(double p) { return det_log1m(p); }
+double wo_det_lfact(uint64_t k) { return det_lfact(k); }
 double wo_det_exp(double x) { return det_exp(x); }
 
 /* ------------------------------------------------------------------------ */

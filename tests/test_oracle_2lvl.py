@@ -58,7 +58,11 @@ def test_single_group_is_alg2(n):
         assert np.array_equal(O.sample_2lvl(t, 3000, 9, 4), O.sample(tab.thr, tab.alias, tab.Qp, 3000, 9, 4))
 
 
-@pytest.mark.parametrize("n,G,seed", [(7, 2, 1), (30, 3, 2), (100, 4, 3), (5000, 2048, 4), (9000, 64, 5)])
+GROUP_CASES = [(7, 2, 1), (30, 3, 2), (100, 4, 3), (5000, 2048, 4), (9000, 64, 5)]
+PROB_CASES = [(7, 2, 11), (13, 3, 12), (40, 4, 13), (3000, 2048, 14)]
+
+
+@pytest.mark.parametrize("n,G,seed", GROUP_CASES)
 def test_every_group_is_an_alias_table(n, G, seed):
     w = WL.u32_uniform(n, seed)
     w[::7] = 0  # zero weights: light, never sampled
@@ -100,7 +104,7 @@ def _exact_item_probabilities(t):
     return probs
 
 
-@pytest.mark.parametrize("n,G,seed", [(7, 2, 11), (13, 3, 12), (40, 4, 13), (3000, 2048, 14)])
+@pytest.mark.parametrize("n,G,seed", PROB_CASES)
 def test_item_probabilities_are_the_weights(n, G, seed):
     w = WL.f32_zipf(n, 1.2, seed)
     w[3] = 0.0

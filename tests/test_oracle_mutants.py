@@ -8,6 +8,8 @@ import numpy as np
 import pytest
 
 from oracle import wrs_oracle as O
+from tests import test_oracle_2lvl as TL
+from tests import test_oracle_osnd as OS
 from tests import test_oracle_pins as P
 from tests import test_oracle_psaplus as PP
 
@@ -84,13 +86,84 @@ def _pp_alias_tables():
 PP_PINS = [PP.test_hand_examples, PP.test_exhaustive_small, _pp_alias_tables]
 
 
+# Two-level tables (Sec. 6, Alg. 2 per group), caught by the two-level pins.
+# Every mutant keeps each index inside its level, so a mutated oracle cannot
+# read out of bounds.
+TL_MUTANTS = {
+    # a group's aliases stay local to the group instead of level-wide indices
+    "tl_alias_local": ("            for (m = 0; m < ng; ++m) al[off + b0 + m] += (uint32_t)b0;\n", ""),
+    # the next level's weight of a group is its first member's instead of the group total
+    "tl_next_weight": ("st128(next + 2 * g, S);", "st128(next + 2 * g, ld128(w + 2 * b0));"),
+    # the coin of every group uses the denominator of the level's first group
+    "tl_coin_group0": ("g = ((uint64_t)(((u128)v * qp[goffs[lv] + g]) >> 64) < thr[b]) ? base + r : al[b];",
+                       "g = ((uint64_t)(((u128)v * qp[goffs[lv]]) >> 64) < thr[b]) ? base + r : al[b];"),
+}
+
+
+def _tl_pins():
+    for n, G, seed in TL.GROUP_CASES:
+        TL.test_every_group_is_an_alias_table(n, G, seed)
+
+
+def _tl_probabilities():
+    for n, G, seed in TL.PROB_CASES:
+        TL.test_item_probabilities_are_the_weights(n, G, seed)
+
+
+TL_PINS = [_tl_pins, _tl_probabilities, TL.test_samples_follow_the_weights]
+
+
+# OS-ND (Sec. 5 output-sensitive sampling, Sec. 10 base case), caught by the
+# OS-ND pins.  Mutants that could make the inversion loop run towards n = 10^12
+# steps (an exp or log1m that returns too small a P(X = 0)) are left out: they
+# would not end in a test's time.
+OS_MUTANTS = {
+    # symmetry: the deviate drawn for 1 - p is returned as the one for p
+    "os_flip_dropped": ("return flip ? n - x : x;", "return x;"),
+    # the left child's weight counts the middle member too
+    "os_split_mid": ("if (i < mid) wl += w;", "if (i <= mid) wl += w;"),
+    # inversion: the pmf ratio drops its "- p/q" term
+    "os_inversion_ratio": ("r *= (x <= 40 ? a * DET_INV[x] : a / (double)x) - s;",
+                           "r *= (x <= 40 ? a * DET_INV[x] : a / (double)x);"),
+    # BTRS: log(q/p) in place of log(p/q) in the acceptance test
+    "os_btrs_lpq": ("lpq = det_log(p / q);", "lpq = det_log(q / p);"),
+    # base case: every group's coin uses the level's first denominator
+    "os_base_coin_group0": ("x->qp[x->goffs[level] + g]", "x->qp[x->goffs[level]]"),
+    # log: range reduction moves the exponent the wrong way
+    "log_reduction": ("if (f > 1.4142135623730951) { f = f * 0.5; e += 1; }",
+                      "if (f > 1.4142135623730951) { f = f * 0.5; e -= 1; }"),
+    # log(1 - p): sign of the series dropped
+    "log1m_sign": ("return -p * acc;", "return p * acc;"),
+    # Stirling: (k + 1/2) log z written as k log z
+    "lfact_half": ("((double)k + 0.5) * det_log(z) - z", "(double)k * det_log(z) - z"),
+    # Stirling: the 1/(12 z) ... correction dropped
+    "lfact_corr": ("0.5 * det_log(6.283185307179586) + corr;", "0.5 * det_log(6.283185307179586);"),
+}
+
+
+def _os_laws():
+    for n, num, den in OS.LAW_CASES:
+        OS.test_binomial_law(n, num, den)
+
+
+def _os_counts():
+    for k in OS.COUNT_CASES:
+        OS.test_osnd_counts_add_up(k)
+
+
+OS_PINS = [OS.test_series_log_exp, OS.test_series_log1m, OS.test_series_lfact, OS.test_binomial_edges,
+           OS.test_binomial_tiny_p_huge_n, _os_laws, _os_counts, OS.test_osnd_is_multinomial,
+           OS.test_osnd_small_k_follows_the_weights]
+
+
 def _run_mutant(old, new, pins, tmp_path):
     src = open(SRC).read()
     assert src.count(old) == 1, "mutation site not found exactly once"
     mutated = tmp_path / "mutant.c"
     mutated.write_text(src.replace(old, new))
     so = str(tmp_path / "libmutant.so")
-    subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-o", so, str(mutated), "-lm"])
+    subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-shared", "-fPIC", "-o", so,
+                           str(mutated), "-lm"])
     caught = []
     with O.use_library(so):
         for pin in pins:
@@ -107,20 +180,19 @@ def test_every_planted_psa_plus_mistake_is_caught(name, tmp_path):
     assert _run_mutant(old, new, PP_PINS, tmp_path), f"mutant {name} passed every PSA+ pin"
 
 
+@pytest.mark.parametrize("name", sorted(TL_MUTANTS))
+def test_every_planted_two_level_mistake_is_caught(name, tmp_path):
+    old, new = TL_MUTANTS[name]
+    assert _run_mutant(old, new, TL_PINS, tmp_path), f"mutant {name} passed every two-level pin"
+
+
+@pytest.mark.parametrize("name", sorted(OS_MUTANTS))
+def test_every_planted_osnd_mistake_is_caught(name, tmp_path):
+    old, new = OS_MUTANTS[name]
+    assert _run_mutant(old, new, OS_PINS, tmp_path), f"mutant {name} passed every OS-ND pin"
+
+
 @pytest.mark.parametrize("name", sorted(MUTANTS))
 def test_every_planted_mistake_is_caught(name, tmp_path):
     old, new = MUTANTS[name]
-    src = open(SRC).read()
-    assert src.count(old) == 1, f"mutation site for {name} not found exactly once"
-    mutated = tmp_path / "mutant.c"
-    mutated.write_text(src.replace(old, new))
-    so = str(tmp_path / "libmutant.so")
-    subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-o", so, str(mutated)])
-    caught = []
-    with O.use_library(so):
-        for pin in PINS:
-            try:
-                pin()
-            except Exception:  # a failed assertion or an oracle error both count as caught
-                caught.append(pin.__name__)
-    assert caught, f"mutant {name} passed every pin"
+    assert _run_mutant(old, new, PINS, tmp_path), f"mutant {name} passed every pin"

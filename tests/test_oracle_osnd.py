@@ -29,6 +29,17 @@ def test_series_log1m():
         assert abs(O.det_log1m(p) - want) <= 4e-16 * abs(want), p
 
 
+def test_series_lfact():
+    """log(k!) of the BTRS acceptance test against the library's lgamma: exact
+    product below 10; above, Stirling's series to the z^-7 term, whose error
+    is below the first omitted term 1 / (1188 z^9), z = k + 1."""
+    for k in list(range(40)) + [100, 1000, 10 ** 6, 10 ** 9, 10 ** 12, 2 ** 53]:
+        want, z = math.lgamma(k + 1), k + 1.0
+        bound = (1.0 / (1188.0 * z ** 9) if k >= 10 else 0.0) + 1e-15 * abs(want)
+        assert abs(O.det_lfact(k) - want) <= bound, k
+    assert O.det_lfact(0) == 0.0 and O.det_lfact(1) == 0.0
+
+
 def test_binomial_tiny_p_huge_n():
     """n p = 3 with n = 10^12: P(X = 0) = e^-3 to 1e-12 relative; the
     frequencies of 0 and of small values follow the Poisson limit."""
@@ -61,7 +72,7 @@ def _chi2(draws, n, p):
     return chi, int(keep.sum())
 
 
-@pytest.mark.parametrize("n,num,den", [
+LAW_CASES = [
     (5, 3, 10),            # inversion
     (30, 1, 5),            # inversion, n p = 6
     (200, 3, 10),          # BTRS
@@ -70,7 +81,11 @@ def _chi2(draws, n, p):
     (10 ** 6, 1, 10 ** 4), # BTRS, n p = 100
     (10 ** 9, 37, 100),    # BTRS, large n
     (10 ** 6, 3, 10 ** 6), # inversion, n p = 3
-])
+]
+COUNT_CASES = [1, 7, 127, 128, 1000, 10 ** 6, 10 ** 12]
+
+
+@pytest.mark.parametrize("n,num,den", LAW_CASES)
 def test_binomial_law(n, num, den):
     N = 20_000
     draws = np.array([O.binomial(n, num, den, 11, node) for node in range(N)], dtype=np.int64)
@@ -95,7 +110,7 @@ def _table(n, s, seed, zeros=()):
     return qz, O.build_2lvl(qz)
 
 
-@pytest.mark.parametrize("k", [1, 7, 127, 128, 1000, 10 ** 6, 10 ** 12])
+@pytest.mark.parametrize("k", COUNT_CASES)
 def test_osnd_counts_add_up(k):
     qz, t = _table(5000, 1.2, 3, zeros=(10, 4999))
     items, counts = O.os_nd(qz, t, k, 5, 2)
