@@ -785,7 +785,9 @@ static uint64_t os_binomial(uint64_t n, u128 num, u128 den, os_rng *rng)
             while (u > r) {
                 u -= r;
                 x++;
-                if (x > n) break;
+                /* with r = 0 every later term is 0 and u stays above it until */
+                /* x > n: the try fails either way, so it stops here           */
+                if (x > n || r == 0.0) { x = n + 1; break; }
                 r *= (x <= 40 ? a * DET_INV[x] : a / (double)x) - s;
             }
             if (x <= n) break;
@@ -933,6 +935,8 @@ uint64_t wo_binomial(uint64_t n, uint64_t num, uint64_t den, uint64_t seed, uint
 double wo_det_log(double x) { return det_log(x); }
 double wo_det_log1m(double p) { return det_log1m(p); }
 double wo_det_lfact(uint64_t k) { return det_lfact(k); }
+double wo_det_u128_to_double(uint64_t lo, uint64_t hi) { return det_u128_to_double(((u128)hi << 64) | lo); }
+double wo_det_ldexp(double x, int e) { return det_ldexp(x, e); }
 double wo_det_exp(double x) { return det_exp(x); }
 
 /* ------------------------------------------------------------------------ */

@@ -97,6 +97,10 @@ def lib():
             L.wo_det_log1m.restype = ctypes.c_double
             L.wo_det_lfact.argtypes = [U64]
             L.wo_det_lfact.restype = ctypes.c_double
+            L.wo_det_u128_to_double.argtypes = [U64, U64]
+            L.wo_det_u128_to_double.restype = ctypes.c_double
+            L.wo_det_ldexp.argtypes = [ctypes.c_double, INT]
+            L.wo_det_ldexp.restype = ctypes.c_double
             L.wo_psa_plus.argtypes = [U64, P, P, U64, P, P, P]
             L.wo_psa_plus.restype = INT
             _lib = L
@@ -118,7 +122,8 @@ class use_library:
         for name in ("wo_quantize", "wo_sweep", "wo_vose", "wo_psa", "wo_vose_f64", "wo_encode",
                      "wo_philox4x32_10", "wo_sample", "wo_sample_at", "wo_2lvl_levels", "wo_2lvl_build",
                      "wo_2lvl_sample", "wo_2lvl_sample_at", "wo_os_nd", "wo_binomial", "wo_det_log",
-                     "wo_det_exp", "wo_det_log1m", "wo_det_lfact", "wo_psa_plus"):
+                     "wo_det_exp", "wo_det_log1m", "wo_det_lfact", "wo_det_u128_to_double", "wo_det_ldexp",
+                     "wo_psa_plus"):
             f, g = getattr(L, name), getattr(self.saved, name)
             f.argtypes, f.restype = g.argtypes, g.restype
         with _lock:
@@ -384,6 +389,15 @@ def det_exp(x: float) -> float:
 
 def det_log1m(p: float) -> float:
     return float(lib().wo_det_log1m(p))
+
+
+def det_u128_to_double(x: int) -> float:
+    """The binomial's probability conversion: nearest binary64 to x < 2^128."""
+    return float(lib().wo_det_u128_to_double(x & (2 ** 64 - 1), x >> 64))
+
+
+def det_ldexp(x: float, e: int) -> float:
+    return float(lib().wo_det_ldexp(x, e))
 
 
 def det_lfact(k: int) -> float:

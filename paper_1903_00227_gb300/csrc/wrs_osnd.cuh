@@ -158,10 +158,12 @@ __device__ uint64_t os_binomial(uint64_t n, u128 num, u128 den, OsRng &rng)
         for (;;) {
             double u = os_unif(rng), r = r0;
             x = 0;
+            // once the pmf terms have underflowed to 0 the try cannot end
+            // before x > n: it is abandoned at once (same outcome, same draws)
             while (u > r) {
                 u -= r;
                 x++;
-                if (x > n) break;
+                if (x > n || r == 0.0) { x = n + 1; break; }
                 r *= (x <= 40 ? a * kOsInv[x] : a / (double)x) - s;
             }
             if (x <= n) break;

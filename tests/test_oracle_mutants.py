@@ -114,9 +114,8 @@ TL_PINS = [_tl_pins, _tl_probabilities, TL.test_samples_follow_the_weights]
 
 
 # OS-ND (Sec. 5 output-sensitive sampling, Sec. 10 base case), caught by the
-# OS-ND pins.  Mutants that could make the inversion loop run towards n = 10^12
-# steps (an exp or log1m that returns too small a P(X = 0)) are left out: they
-# would not end in a test's time.
+# OS-ND pins.  An inversion try ends once its pmf terms underflow, so a mutant
+# whose P(X = 0) is too small only makes more tries fail.
 OS_MUTANTS = {
     # symmetry: the deviate drawn for 1 - p is returned as the one for p
     "os_flip_dropped": ("return flip ? n - x : x;", "return x;"),
@@ -138,6 +137,15 @@ OS_MUTANTS = {
     "lfact_half": ("((double)k + 0.5) * det_log(z) - z", "(double)k * det_log(z) - z"),
     # Stirling: the 1/(12 z) ... correction dropped
     "lfact_corr": ("0.5 * det_log(6.283185307179586) + corr;", "0.5 * det_log(6.283185307179586);"),
+    # p's conversion: ties rounded up instead of to even
+    "u128_ties_up": ("if (rem > half || (rem == half && (m & 1))) {", "if (rem >= half) {"),
+    # power-of-two scaling: exponent bias off by one
+    "ldexp_bias": ("t.u = (uint64_t)(e + 1023) << 52;", "t.u = (uint64_t)(e + 1022) << 52;"),
+    # exp: range reduction adds k ln 2 instead of subtracting it
+    "exp_reduction": ("r = x - kd * 0.6931471805599453;", "r = x + kd * 0.6931471805599453;"),
+    # exp: the Taylor terms' 1/j taken as 1/(j + 1)
+    "exp_term_index": ("for (j = 20; j >= 1; --j) acc = acc * (r * DET_INV[j]) + 1.0;",
+                       "for (j = 20; j >= 1; --j) acc = acc * (r * DET_INV[j + 1]) + 1.0;"),
 }
 
 
@@ -151,7 +159,8 @@ def _os_counts():
         OS.test_osnd_counts_add_up(k)
 
 
-OS_PINS = [OS.test_series_log_exp, OS.test_series_log1m, OS.test_series_lfact, OS.test_binomial_edges,
+OS_PINS = [OS.test_series_log_exp, OS.test_series_log1m, OS.test_series_lfact,
+           OS.test_u128_to_double_rounds_to_nearest_even, OS.test_ldexp_is_exact_scaling, OS.test_binomial_edges,
            OS.test_binomial_tiny_p_huge_n, _os_laws, _os_counts, OS.test_osnd_is_multinomial,
            OS.test_osnd_small_k_follows_the_weights]
 

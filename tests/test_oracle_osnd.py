@@ -40,6 +40,32 @@ def test_series_lfact():
     assert O.det_lfact(0) == 0.0 and O.det_lfact(1) == 0.0
 
 
+def test_u128_to_double_rounds_to_nearest_even():
+    """The conversion that forms p = num / den: the nearest binary64 with
+    ties to even, which is what Python's int -> float conversion guarantees."""
+    rng = np.random.default_rng(17)
+    xs = [0, 1, 2 ** 53 - 1, 2 ** 53, 2 ** 53 + 1, 2 ** 53 + 2, 2 ** 53 + 3, 2 ** 54 + 2, 2 ** 54 + 6,
+          2 ** 64 - 1, 2 ** 64, 2 ** 95, 2 ** 95 + 2 ** 42, 2 ** 95 + 3 * 2 ** 42, 2 ** 128 - 1, 2 ** 127 + 2 ** 74]
+    for bits in (54, 60, 64, 80, 96, 110, 128):
+        for _ in range(200):
+            x = int(rng.integers(0, 2 ** 62)) | (int(rng.integers(0, 2 ** 62)) << 62) | (int(rng.integers(0, 16)) << 124)
+            x &= (1 << bits) - 1
+            xs.append(x)
+            sh = max(bits - 53, 1)
+            xs.append((x >> sh << sh) | (1 << (sh - 1)))  # a tie at this width
+    for x in xs:
+        assert O.det_u128_to_double(x) == float(x), hex(x)
+
+
+def test_ldexp_is_exact_scaling():
+    """The power-of-two scaling of exp and of the u128 conversion, including
+    results in the subnormal range (one rounding, ties to even)."""
+    for x in (1.0, 1.5, 0.75, 1.9999999999999998, 2.0 ** 52 + 1):
+        for e in (-1126, -1074, -1073, -1060, -1022, -1000, -999, -1, 0, 1, 75, 970, 1000, 1023):
+            if math.frexp(x)[1] + e <= 1024:
+                assert O.det_ldexp(x, e) == math.ldexp(x, e), (x, e)
+
+
 def test_binomial_tiny_p_huge_n():
     """n p = 3 with n = 10^12: P(X = 0) = e^-3 to 1e-12 relative; the
     frequencies of 0 and of small values follow the Poisson limit."""
