@@ -62,17 +62,17 @@ def check_alias_table(q: list[int], Q: int, bw: list[int], alias: list[int]) -> 
         assert mass[i] == n * q[i], (i, mass[i], n * q[i])
 
 
-def coin_heads(thr: int, Qp: int) -> int:
-    """#{v in [0, 2^64) : floor(v * Qp / 2^64) < thr}."""
+def coin_heads(thr: int, Qp: int, bits: int = 64) -> int:
+    """#{v in [0, 2^bits) : floor(v * Qp / 2^bits) < thr}."""
     if thr >= Qp:
-        return TWO64
-    return -((-thr * TWO64) // Qp)  # ceil(thr * 2^64 / Qp)
+        return 1 << bits
+    return -((-thr << bits) // Qp)  # ceil(thr * 2^bits / Qp)
 
 
-def bucket_count(r: int, n: int) -> int:
-    """#{u in [0, 2^64) : floor(u * n / 2^64) = r}."""
-    def first(x):
-        return -((-x * TWO64) // n)
+def bucket_count(r: int, n: int, bits: int = 64) -> int:
+    """#{u in [0, 2^bits) : floor(u * n / 2^bits) = r}."""
+    def first(x):  # the least u with floor(u * n / 2^bits) >= x
+        return -((-x << bits) // n)
     return first(r + 1) - first(r)
 
 

@@ -70,3 +70,33 @@ def test_n1e8_table_probabilities_and_chi_square(kind, s, seed):
     np.add.at(mass, al[other], 1.0 - prob[other])
     rel64 = np.abs(mass[nz] / N - p_exact[nz]) / p_exact[nz]
     print(f"{kind}: GPU max rel err {rel.max():.3e}; binary64 Vose max rel err {rel64.max():.3e}; chi2 z {z:.2f}")
+
+
+def test_bucket_index_uniformity():
+    """All-equal weights: every bucket is full with itself as alias (the
+    all-equal case of Alg. 2), so each draw returns its bucket index and 10^9
+    GPU draws test the multiply-shift bucket choice alone: a chi-square over
+    10^5 bins of 1000 consecutive buckets (each bucket is hit by floor or ceil
+    of 2^64 / n of the 2^64 words, a bias below 10^-10)."""
+    w_dev = torch.full((N,), 3, dtype=torch.int32, device="cuda")
+    with wrs.AliasTable(N) as t:
+        t.build(w_dev)
+        assert t.status() == wrs.OK
+        thr, alias, _ = t.download()
+        info = t.info()
+        assert info.Q == 3 * N and info.shift == 0
+        assert np.array_equal(alias, np.arange(N, dtype=np.uint32))
+        assert np.all(thr == np.uint64(info.qp))  # a full bucket's coin always keeps it
+        k = 1_000_000_000
+        out = t.sample(k, seed=77, stream_id=5)
+        bins = N // 1000
+        counts = torch.zeros(bins, dtype=torch.int64, device="cuda")
+        for i in range(0, k, 100_000_000):
+            counts += torch.bincount(out[i:i + 100_000_000].long() // 1000, minlength=bins)
+        counts = counts.cpu().numpy().astype(np.float64)
+    assert counts.sum() == k
+    e = k / bins
+    chi2 = float(((counts - e) ** 2 / e).sum())
+    df = bins - 1
+    z = (chi2 - df) / np.sqrt(2 * df)
+    assert abs(z) < 5, (chi2, df, z)

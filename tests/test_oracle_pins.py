@@ -316,6 +316,28 @@ def test_sampler_n1_and_full_buckets_reduce_to_multiply_shift():
         assert out[s] == (u * n) >> 64  # Lemire's multiply-shift bucket choice
 
 
+def test_closed_form_counts_match_brute_force():
+    """The closed forms behind the exact query distribution, checked by
+    counting every word of a 12-bit analogue: how many u pick bucket r under
+    multiply-shift (always floor or ceil of 2^bits / n), and how many v pass
+    the coin floor(v * Qp / 2^bits) < thr."""
+    bits = 12
+    u = np.arange(1 << bits, dtype=np.int64)
+    for n in list(range(1, 130)) + [1000, 4095, 4096]:
+        got = np.bincount((u * n) >> bits, minlength=n)
+        want = [C.bucket_count(r, n, bits) for r in range(n)]
+        assert got.tolist() == want, n
+        assert set(want) <= {(1 << bits) // n, -(-(1 << bits) // n)}, n
+    for Qp in (1, 2, 3, 7, 100, 4095, 4096, 5000):
+        for thr in sorted({0, 1, 2, Qp // 3, Qp // 2, Qp - 1, Qp, Qp + 1}):
+            assert int(((u * Qp) >> bits < thr).sum()) == C.coin_heads(thr, Qp, bits), (Qp, thr)
+    # at the full width every bucket count is still floor or ceil of 2^64 / n
+    for n in (3, 10 ** 6, 10 ** 9, 2 ** 32 - 1):
+        lo, hi = (1 << 64) // n, -(-(1 << 64) // n)
+        for r in (0, 1, n // 2, n - 1):
+            assert C.bucket_count(r, n) in (lo, hi)
+
+
 def test_sampler_tails_take_the_alias():
     n = 37
     thr = np.zeros(n, np.uint64)
