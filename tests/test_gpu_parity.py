@@ -180,6 +180,36 @@ def test_unaligned_weight_pointer():
     assert np.array_equal(thr, tab.thr) and np.array_equal(alias, tab.alias)
 
 
+def test_concurrent_tables_on_separate_streams():
+    """Four table objects built and sampled on four CUDA streams with nothing
+    ordering one stream against another: table objects share no state, so
+    each table and its samples equal the oracle's for its own weights."""
+    ws = [WL.f32_zipf(3 * TILE + 7 + 1001 * i, 1.0 + 0.25 * i, 40 + i) for i in range(3)]
+    ws.append(WL.u32_uniform(5 * TILE + 3, 44))
+    k = 100_003
+    dev = [G.to_device(w) for w in ws]
+    outs = [torch.empty(k, dtype=torch.int32, device="cuda") for _ in ws]
+    streams = [torch.cuda.Stream() for _ in ws]
+    tables = [wrs.AliasTable(len(w)) for w in ws]
+    torch.cuda.synchronize()
+    try:
+        for t, d, st in zip(tables, dev, streams):
+            t.build(d, stream=st)
+        for i, (t, st) in enumerate(zip(tables, streams)):
+            t.sample(k, 70 + i, i, out=outs[i], stream=st)
+        torch.cuda.synchronize()
+        for i, (w, t) in enumerate(zip(ws, tables)):
+            qz, tab = O.build_table(w)
+            assert t.status() == wrs.OK
+            thr, alias, _ = t.download()
+            assert np.array_equal(thr, tab.thr) and np.array_equal(alias, tab.alias), i
+            got = outs[i].cpu().numpy().view(np.uint32)
+            assert np.array_equal(got, O.sample(tab.thr, tab.alias, tab.Qp, k, 70 + i, i)), i
+    finally:
+        for t in tables:
+            t.free()
+
+
 def test_host_buffer_entry_points():
     w = WL.f32_uniform(20_000, 8)
     qz, tab = O.build_table(w)
