@@ -83,6 +83,10 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=100_000,
                     help="requests of the serving workload (0: skip it)")
     ap.add_argument("--serve-rate", type=float, default=20_000.0, help="Poisson arrival rate, requests/s")
+    ap.add_argument("--serve-loads", default="",
+                    help="comma-separated fractions of the plain path's saturation rate to offer in a load "
+                         "sweep after the serving run (empty: no sweep)")
+    ap.add_argument("--serve-sweep-requests", type=int, default=20_000, help="requests per load-sweep point")
     return ap.parse_args()
 
 
@@ -658,6 +662,23 @@ def run_serving(args, torch):
            "served": S.summarize(served, reqs), "plain": S.summarize(plain, reqs),
            "identical_samples": same, "table_objects_reserved": reserved, "reserve_seconds": setup_s,
            "objects_created_total": srv.cache.created, "objects_freed": srv.cache.freed}
+    loads = [float(x) for x in args.serve_loads.split(",") if x.strip()]
+    if loads:
+        # offered loads below the plain path's saturation rate, which the run
+        # above measured (its arrivals outpace the plain path), so that both
+        # paths are compared at a load each can sustain
+        sat = out["plain"]["requests_per_s"]
+        points = []
+        for f in loads:
+            rq = S.request_stream(args.serve_sweep_requests, rate=f * sat, seed=6)
+            srv.cache.clear_resident()
+            a = srv.run(rq)
+            srv.cache.clear_resident()
+            b = srv.run_plain(rq)
+            points.append({"load": f, "rate": f * sat, "served": S.summarize(a, rq), "plain": S.summarize(b, rq),
+                           "identical_samples": bool((a["checksum"] == b["checksum"]).all())})
+        out["load_sweep"] = {"plain_saturation_rate": sat, "requests_per_point": args.serve_sweep_requests,
+                             "points": points}
     srv.close()
     return out
 
