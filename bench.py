@@ -22,7 +22,9 @@ workload.  The other rows ride on the same line: ``psa_plus`` (PSA+ builds),
 ``two_level`` (two-level tables, with ``os_nd`` output-sensitive sampling),
 ``many_tables`` (4096 tables built and sampled in one CUDA graph against one
 table at a time) and ``serving`` (a Poisson request stream against one
-request at a time), each with the oracle timed beside it where it applies.
+request at a time; ``--serve-loads`` adds ``serving.load_sweep``, both paths
+at fractions of the plain path's saturation rate), each with the oracle timed
+beside it where it applies.
 
 ``--impl reference`` times the CPU oracle itself (the reference arm of this
 repository) on bounded samples of the same workload.
