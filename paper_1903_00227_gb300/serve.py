@@ -253,6 +253,7 @@ class Server:
         self.slots = [_Slot(torch, tick_requests, tick_samples) for _ in range(max_inflight)]
         self.last_use = {}  # id(table object) -> event of the last tick that read it
         self.ptrs = {}      # id(table object) -> (buckets, header)
+        self.rebuilds = 0   # sample-only requests of the current run whose table had been evicted
 
     # -- table objects
     def _create(self, cap):
@@ -327,6 +328,7 @@ class Server:
         inflight = collections.deque()
         nxt = 0
         pending = collections.deque()  # arrived, not yet admitted
+        ev0, self.rebuilds = self.cache.evictions, 0
         t0 = time.perf_counter()
         ticks = 0
 
@@ -372,7 +374,7 @@ class Server:
                     time.sleep(min(delay, 0.001))
         wall = time.perf_counter() - t0
         return {"latency": lat, "checksum": sums, "outputs": outs, "wall": wall, "ticks": ticks,
-                "evictions": self.cache.evictions}
+                "evictions": self.cache.evictions - ev0, "rebuilds": self.rebuilds}
 
     def _issue(self, slot, pending):
         """Admit pending requests into `slot` and launch its device work."""
@@ -392,6 +394,8 @@ class Server:
                 if r is None:
                     break  # no memory until in-flight ticks complete
                 t, w = r
+                if not req.build:
+                    self.rebuilds += 1
                 slot.keep.append(w)
                 ev = torch.cuda.Event()
                 ev.record(stream)
@@ -438,6 +442,7 @@ class Server:
         outs = [None] * N if keep_outputs else None
         slot = self.slots[0]
         s = self.sstream
+        ev0, rebuilds = self.cache.evictions, 0
         t0 = time.perf_counter()
         for req in reqs:
             delay = req.arrival - (time.perf_counter() - t0)
@@ -450,6 +455,7 @@ class Server:
                 if r is None:
                     raise RuntimeError("budget too small for one table")
                 t = r[0]
+                rebuilds += 0 if req.build else 1
             else:
                 t = e[1]
             with torch.cuda.stream(s):
@@ -465,15 +471,17 @@ class Server:
                 outs[req.rid] = seg.copy()
         wall = time.perf_counter() - t0
         return {"latency": lat, "checksum": sums, "outputs": outs, "wall": wall, "ticks": N,
-                "evictions": self.cache.evictions}
+                "evictions": self.cache.evictions - ev0, "rebuilds": rebuilds}
 
 
 def summarize(res, reqs) -> dict:
     lat = res["latency"] * 1e3
     n_build = sum(1 for r in reqs if r.build)
+    n_sample_only = len(reqs) - n_build
     return {"requests": len(reqs), "wall_s": res["wall"], "requests_per_s": len(reqs) / res["wall"],
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "mean_ms": float(lat.mean()), "builds": n_build,
             "gsamples_s": sum(r.k for r in reqs) / res["wall"] / 1e9,
             "gweights_built_s": sum(r.n for r in reqs if r.build) / res["wall"] / 1e9,
-            "ticks": res["ticks"], "evictions": res["evictions"]}
+            "ticks": res["ticks"], "evictions": res["evictions"], "rebuilds": res["rebuilds"],
+            "sample_hit_rate": 1.0 - res["rebuilds"] / max(n_sample_only, 1)}

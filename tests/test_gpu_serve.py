@@ -40,6 +40,9 @@ def test_served_equals_plain_and_oracle(payload):
         assert served["ticks"] > 3, "requests must be batched over several overlapping ticks"
         srv.cache.clear_resident()
         plain = srv.run_plain(reqs, keep_outputs=True)
+        # every table fits the budget: nothing evicted, every sample-only request hits
+        assert served["evictions"] == plain["evictions"] == 0
+        assert served["rebuilds"] == plain["rebuilds"] == 0
     finally:
         srv.close()
     for r in reqs:
@@ -55,8 +58,10 @@ def test_tiny_budget_evicts_and_rebuilds_same_results(payload):
     big = S.Server(budget=2 << 30, max_inflight=1, tick_requests=1, tick_samples=1 << 18, payload=payload)
     try:
         a = small.run(reqs, keep_outputs=True)
-        assert a["evictions"] > 10
+        assert a["evictions"] > 10 and a["rebuilds"] > 0
+        assert S.summarize(a, reqs)["sample_hit_rate"] < 1.0
         b = big.run(reqs, keep_outputs=True)
+        assert b["evictions"] == 0 and b["rebuilds"] == 0
     finally:
         small.close()
         big.close()
