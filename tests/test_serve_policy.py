@@ -92,3 +92,19 @@ def test_cache_frees_smaller_objects_for_a_large_table():
     o, cls = c.acquire(12, Obj, freed.append)
     assert cls == 12 and len(freed) == 1 and 0 not in c.resident and 1 in c.resident
     assert c.used <= c.budget and c.freed == 1
+
+
+def test_summary_counts_per_run():
+    """The summary of one run: latency percentiles, rates and the share of
+    sample-only requests that found their table resident."""
+    reqs = S.request_stream(1000, rate=1000.0, seed=9)
+    n_sample_only = sum(1 for r in reqs if not r.build)
+    lat = np.linspace(0.001, 0.1, len(reqs))
+    res = {"latency": lat, "wall": 2.0, "ticks": 40, "evictions": 12, "rebuilds": n_sample_only // 4}
+    s = S.summarize(res, reqs)
+    assert s["requests"] == 1000 and s["requests_per_s"] == 500.0
+    assert s["builds"] == len(reqs) - n_sample_only
+    assert s["p50_ms"] == np.percentile(lat * 1e3, 50) and s["p99_ms"] == np.percentile(lat * 1e3, 99)
+    assert s["evictions"] == 12 and s["rebuilds"] == n_sample_only // 4
+    assert abs(s["sample_hit_rate"] - (1 - (n_sample_only // 4) / n_sample_only)) < 1e-12
+    assert s["gsamples_s"] == sum(r.k for r in reqs) / 2.0 / 1e9
