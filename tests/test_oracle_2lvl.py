@@ -37,6 +37,22 @@ def _level_weights(q_ints, t):
     return out
 
 
+def test_hand_examples():
+    """Two-level tables worked by hand (tests/golden/two_level_hand_examples.json):
+    three levels of groups of two, with and without zero weights."""
+    import json
+    import os
+
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "two_level_hand_examples.json")))
+    for ex in g["examples"]:
+        qz = O.quantize(np.array(ex["w"], np.uint32))
+        t = O.build_2lvl(qz, ex["G"])
+        assert list(t.sizes) == ex["levels"], ex["name"]
+        assert t.thr.tolist() == ex["thr"], ex["name"]
+        assert t.alias.tolist() == ex["alias"], ex["name"]
+        assert t.qp.tolist() == ex["qp"] and not t.shift.any(), ex["name"]
+
+
 def test_level_sizes():
     assert O.levels_2lvl(1) == [1]
     assert O.levels_2lvl(2048) == [2048]

@@ -110,7 +110,7 @@ def _tl_probabilities():
         TL.test_item_probabilities_are_the_weights(n, G, seed)
 
 
-TL_PINS = [_tl_pins, _tl_probabilities, TL.test_samples_follow_the_weights]
+TL_PINS = [TL.test_hand_examples, _tl_pins, _tl_probabilities, TL.test_samples_follow_the_weights]
 
 
 # OS-ND (Sec. 5 output-sensitive sampling, Sec. 10 base case), caught by the
