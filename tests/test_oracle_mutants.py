@@ -159,10 +159,15 @@ def _os_counts():
         OS.test_osnd_counts_add_up(k)
 
 
+def _os_single_weight():
+    for n in (2047, 5000):
+        OS.test_osnd_single_nonzero_weight(n)
+
+
 OS_PINS = [OS.test_series_log_exp, OS.test_series_log1m, OS.test_series_lfact,
            OS.test_u128_to_double_rounds_to_nearest_even, OS.test_ldexp_is_exact_scaling, OS.test_binomial_edges,
            OS.test_binomial_tiny_p_huge_n, _os_laws, _os_counts, OS.test_osnd_is_multinomial,
-           OS.test_osnd_small_k_follows_the_weights]
+           OS.test_osnd_small_k_follows_the_weights, _os_single_weight]
 
 
 def _run_mutant(old, new, pins, tmp_path):

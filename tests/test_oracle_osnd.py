@@ -151,6 +151,27 @@ def test_osnd_counts_add_up(k):
         assert len(items) <= qz.n  # large counts: each item at most once (descent to the leaves)
 
 
+@pytest.mark.parametrize("n", [1, 2047, 5000, 2048 * 2048 + 5])
+def test_osnd_single_nonzero_weight(n):
+    """All the weight on one item: every sample is that item, so a descent
+    hands all k to it (one pair (i, k)), and where the item's group takes the
+    base case (fewer than 128 samples, at least half as many items, Sec. 10)
+    its k queries all land on it (k pairs (i, 1))."""
+    i = n // 3
+    w = np.zeros(n, np.float32)
+    w[i] = 0.75
+    qz = O.quantize(w)
+    t = O.build_2lvl(qz)
+    G = t.G
+    n_group = min(G, n - i // G * G)  # members of the item's group
+    for k in (1, 50, 127, 128, 10 ** 6, 10 ** 12):
+        items, counts = O.os_nd(qz, t, k, 3, 1)
+        if k < 128 and 2 * n_group >= k:
+            assert items.tolist() == [i] * k and counts.tolist() == [1] * k, k
+        else:
+            assert items.tolist() == [i] and counts.tolist() == [k], k
+
+
 def test_osnd_is_multinomial():
     qz, t = _table(3000, 1.0, 4)
     k = 10 ** 7
