@@ -74,6 +74,14 @@ PP_MUTANTS = {
     # a packed heavy item's overflow goes to itself instead of the next heavy item
     "pp_heavy_alias_self": ("                    put(bw, al, j, w, jn);\n                    done[j - t0] = 1;",
                             "                    put(bw, al, j, w, j);\n                    done[j - t0] = 1;"),
+    # the second phase skips leftovers at exactly capacity when looking for its first light item
+    "pp_second_phase_full_not_light": ("    while (i < m && V(i) > Q) ++i;           /* first light */",
+                                       "    while (i < m && V(i) >= Q) ++i;          /* first light */"),
+    # a tile's residual drops the packed light item's weight
+    "pp_residual_drops_light": ("                    w = (w + nq(&in, i)) - Q;", "                    w = w - Q;"),
+    # the next item of a packed heavy is looked up among the lights
+    "pp_next_heavy_is_light": ("                    while (jn < t1 && is_light(&in, jn)) ++jn;",
+                               "                    while (jn < t1 && !is_light(&in, jn)) ++jn;"),
 }
 
 
