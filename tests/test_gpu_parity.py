@@ -145,6 +145,14 @@ def test_all_zero_and_overflow_reported():
     w[1] = np.float32(2.0 ** 100)
     with G.gpu_build(w) as t:
         assert t.status() == wrs.EOVERFLOW
+    # every item fits in 95 bits, the total does not: q = 1 (x 4998), 2^94, 2^94
+    w = np.full(5000, 2.0 ** -10, np.float32)
+    w[1] = w[4000] = np.float32(2.0 ** 84)
+    with G.gpu_build(w) as t:
+        assert t.status() == wrs.EOVERFLOW
+    w[4000] = np.float32(2.0 ** -10)  # Q = 2^94 + 4999 < 2^95: a valid table
+    with G.gpu_build(w) as t:
+        assert t.status() == wrs.OK and t.info().Q == 2 ** 94 + 4999
 
 
 def test_bounded_wait_times_out_and_context_survives():

@@ -43,6 +43,14 @@ MUTANTS = {
     "query_le": ("        heads = (uint64_t)(((u128)v * Qp) >> 64) < thr[r];", "        heads = (uint64_t)(((u128)v * Qp) >> 64) <= thr[r];"),
     # query: bucket from the high word (operands transposed)
     "query_words": ("        r = (uint64_t)(((u128)u * n) >> 64);\n        heads", "        r = (uint64_t)(((u128)v * n) >> 64);\n        heads"),
+    # binary32 decoding: subnormals scaled like normals (2^-150 instead of 2^-149)
+    "subnormal_scale": ("    if (ex == 0) { *m = fr; *e = -149; }", "    if (ex == 0) { *m = fr; *e = -150; }"),
+    # binary32 decoding: the hidden bit of normal numbers dropped
+    "hidden_bit": ("    else { *m = fr | 0x800000u; *e = (int)ex - 150; }", "    else { *m = fr; *e = (int)ex - 150; }"),
+    # binary32 decoding: the sign bit ignored (negative weights accepted)
+    "sign_ignored": ("    if (bits >> 31) return 1;\n", ""),
+    # the running total's range check dropped
+    "range_unchecked": ("            if (bitlen128(Q) > WO_Q_BITS) return WO_EOVERFLOW;\n", ""),
     # encoding: thresholds not shifted like the denominator
     "encode_shift": ("    for (b = 0; b < n; ++b) thr[b] = (uint64_t)(ld128(bw + 2 * b) >> s);", "    for (b = 0; b < n; ++b) thr[b] = (uint64_t)(ld128(bw + 2 * b) >> (s ? s - 1 : 0));"),
 }
@@ -50,6 +58,8 @@ MUTANTS = {
 PINS = [
     P.test_philox_known_answers,
     P.test_quantize_f32_matches_exact_rationals,
+    P.test_quantize_subnormals_exact,
+    P._quantize_rejections,
     P.test_hand_examples,
     P.test_exhaustive_small_sweep_psa_vose_are_alias_tables,
     P.test_exact_query_distribution_equals_definition,
@@ -191,7 +201,7 @@ def _run_mutant(old, new, pins, tmp_path):
         for pin in pins:
             try:
                 pin()
-            except Exception:  # a failed assertion or an oracle error both count as caught
+            except (Exception, pytest.fail.Exception):  # a failed check or an oracle error: caught
                 caught.append(pin.__name__)
     return caught
 

@@ -78,6 +78,27 @@ def test_quantize_f32_matches_exact_rationals():
         assert Fraction(qz.Q) * Fraction(2) ** qz.beta == sum(Fraction(float(x)) for x in w)
 
 
+def test_quantize_subnormals_exact():
+    """Subnormal weights (exponent field 0: no hidden bit, scale 2^-149)
+    beside small normal ones, within the 2^95 range, against exact rationals."""
+    rng = np.random.default_rng(12)
+    sub = rng.integers(1, 1 << 23, size=200).astype(np.float64) * 2.0 ** -149
+    nrm = rng.integers(1 << 23, 1 << 24, size=200).astype(np.float64) * 2.0 ** rng.integers(-149, -90, size=200)
+    for w in (np.array([2.0 ** -149, np.ldexp(0x7FFFFF, -149), 2.0 ** -126, 2.0 ** -100], np.float32),
+              np.concatenate([sub, nrm]).astype(np.float32)):
+        qz = O.quantize(w)
+        q, Q, beta = C.exact_units(w)
+        assert (qz.beta, qz.Q) == (beta, Q)
+        assert [qz.q_int(i) for i in range(len(w))] == q
+
+
+def _quantize_rejections():
+    for bad in (np.nan, np.inf, -1.0, -0.0):
+        test_quantize_rejects_invalid(bad)
+    test_quantize_rejects_all_zero_and_empty()
+    test_quantize_range_limit()
+
+
 @pytest.mark.parametrize("bad", [np.nan, np.inf, -1.0, -0.0])
 def test_quantize_rejects_invalid(bad):
     w = np.ones(8, dtype=np.float32)
@@ -98,8 +119,9 @@ def test_quantize_range_limit():
     # q = 1, 2^94: Q = 2^94 + 1 < 2^95 fits
     ok = np.array([2.0 ** -10, 2.0 ** 84], dtype=np.float32)
     assert O.quantize(ok).Q == 2 ** 94 + 1
-    # q = 1, 2^95, 2^95: beyond the exact range
-    for w in ([2.0 ** -11, 2.0 ** 84, 2.0 ** 84], [2.0 ** -149, 2.0 ** 100]):
+    # q = 1, 2^95, 2^95: beyond the exact range; q = 1, 2^94, 2^94: each item
+    # fits, the total 2^95 + 1 does not
+    for w in ([2.0 ** -11, 2.0 ** 84, 2.0 ** 84], [2.0 ** -149, 2.0 ** 100], [2.0 ** -10, 2.0 ** 84, 2.0 ** 84]):
         with pytest.raises(O.OracleError) as e:
             O.quantize(np.array(w, dtype=np.float32))
         assert e.value.code == O.EOVERFLOW
