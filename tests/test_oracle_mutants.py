@@ -35,6 +35,11 @@ MUTANTS = {
     "beta_no_ctz": ("            if (m && e + ctz32(m) < beta) beta = e + ctz32(m);", "            if (m && e < beta) beta = e;"),
     # Alg. 1: drops b[i].w in the cancellation-avoiding update
     "vose_drop_term": ("(ld128(bw + 2 * (uint64_t)j) + ld128(bw + 2 * (uint64_t)i)) - in.Q", "ld128(bw + 2 * (uint64_t)j) - in.Q"),
+    # Alg. 1: a light bucket names itself instead of the heavy item that fills it
+    "vose_alias_self": ("            i = ls[--nl];\n            al[i] = j; set[i] = 1;",
+                        "            i = ls[--nl];\n            al[i] = i; set[i] = 1;"),
+    # Alg. 1 in binary64: capacity W / (n + 1) instead of W / n
+    "vose_f64_capacity": ("    cap = W / (double)n;", "    cap = W / (double)(n + 1);"),
     # Philox: wrong Weyl constant
     "philox_weyl": ("k0 += 0x9E3779B9u;", "k0 += 0x9E3779B8u;"),
     # Philox: words 1 and 3 swapped in the round
@@ -66,6 +71,7 @@ PINS = [
     P.test_random_tables_invariants_and_psa_identity,
     P.test_psa_splits_satisfy_paper_condition,
     P.test_one_heavy_among_equal_lights_closed_form,
+    P.test_vose_f64_against_exact_probabilities,
     P.test_sampler_n1_and_full_buckets_reduce_to_multiply_shift,
     P.test_sampler_tails_take_the_alias,
     P.test_sampler_coin_with_small_denominator,
