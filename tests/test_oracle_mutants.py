@@ -29,6 +29,12 @@ MUTANTS = {
                      "static int is_light(const wo_in *in, uint64_t k) { return nq(in, k) < in->Q; }"),
     # Alg. 3 split: strict comparison picks the smaller j
     "split_strict": ("    return (u128)s->in->n * sigma <= (u128)np * s->in->Q;", "    return (u128)s->in->n * sigma < (u128)np * s->in->Q;"),
+    # Alg. 3 boundaries: floor(n k / p) instead of ceil(n k / p)
+    "psa_boundary_floor": ("        snp[k] = (uint64_t)(((u128)n * k + p - 1) / p); /* ceil(n*k/p) */",
+                           "        snp[k] = (uint64_t)(((u128)n * k) / p); /* ceil(n*k/p) */"),
+    # Alg. 3 pack: a light bucket names itself instead of the current heavy item
+    "psa_pack_light_self": ("                put(bw, al, s.l[i], nq(&in, s.l[i]), j < s.nh ? s.h[j] : s.l[i]);",
+                            "                put(bw, al, s.l[i], nq(&in, s.l[i]), s.l[i]);"),
     # Alg. 3 split: spill uses the wrong heavy (h[j-1])
     "split_spill_index": ("ld128(s->in->q + 2 * (uint64_t)s->h[j]))", "ld128(s->in->q + 2 * (uint64_t)s->h[j > 0 ? j - 1 : 0]))"),
     # normalisation: beta ignores the trailing zeros of the mantissa
