@@ -124,6 +124,10 @@ TL_MUTANTS = {
     "tl_alias_local": ("            for (m = 0; m < ng; ++m) al[off + b0 + m] += (uint32_t)b0;\n", ""),
     # the next level's weight of a group is its first member's instead of the group total
     "tl_next_weight": ("st128(next + 2 * g, S);", "st128(next + 2 * g, ld128(w + 2 * b0));"),
+    # every level draws with the same key, so the levels' picks are correlated
+    "tl_same_key_each_level": ("        key[0] = (uint32_t)seed + (uint32_t)d * 0x9E3779B9u;\n"
+                               "        key[1] = (uint32_t)(seed >> 32) + (uint32_t)d * 0xBB67AE85u;",
+                               "        key[0] = (uint32_t)seed;\n        key[1] = (uint32_t)(seed >> 32);"),
     # the coin of every group uses the denominator of the level's first group
     "tl_coin_group0": ("g = ((uint64_t)(((u128)v * qp[goffs[lv] + g]) >> 64) < thr[b]) ? base + r : al[b];",
                        "g = ((uint64_t)(((u128)v * qp[goffs[lv]]) >> 64) < thr[b]) ? base + r : al[b];"),
