@@ -15,6 +15,28 @@ from paper_1903_00227_gb300 import wrs
 pytestmark = pytest.mark.gpu
 
 N = int(os.environ.get("WRS_FULLSIZE_N", 10 ** 9))
+# host memory at the peak of a test: the downloaded 16-B buckets plus the
+# oracle's copies of thresholds and aliases (28 GB at n = 10^9)
+HOST_GB_NEEDED = 30.0 * N / 1e9
+
+
+def _host_available_gb():
+    """MemAvailable of this machine in GB, or None where it cannot be read."""
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) * 1024 / 1e9
+    except (OSError, ValueError, IndexError):
+        return None
+    return None
+
+
+@pytest.fixture(autouse=True)
+def _enough_host_memory():
+    avail = _host_available_gb()
+    if avail is not None and avail < HOST_GB_NEEDED:
+        pytest.skip(f"host memory: {avail:.0f} GB available, {HOST_GB_NEEDED:.0f} GB needed at n = {N}")
 
 
 @pytest.mark.parametrize("builder", ["psa", "psa_plus"])
