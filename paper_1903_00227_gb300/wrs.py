@@ -323,6 +323,20 @@ def _dtype_code(t) -> int:
     raise TypeError(f"weights must be float32 or uint32/int32 words, got {t.dtype}")
 
 
+def _require_cuda(x, what: str, min_numel: int = 0, itemsize: int | None = None) -> None:
+    """Refuse, before any launch, what the kernels must not see: a host
+    tensor (its pointer is not device memory), a strided view, too few
+    elements, or elements of the wrong size."""
+    if not x.is_cuda:
+        raise ValueError(f"{what} must be a CUDA tensor")
+    if not x.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    if x.numel() < min_numel:
+        raise ValueError(f"{what} holds {x.numel()} elements, {min_numel} needed")
+    if itemsize is not None and x.element_size() != itemsize:
+        raise ValueError(f"{what} must have {itemsize}-byte elements, not {x.element_size()}")
+
+
 def _stream_handle(stream) -> int:
     import torch
 
@@ -343,7 +357,7 @@ class AliasTable:
 
     def build(self, weights, stream=None) -> "AliasTable":
         """weights: contiguous CUDA tensor of float32 or uint32/int32 words."""
-        assert weights.is_cuda and weights.is_contiguous()
+        _require_cuda(weights, "weights")
         n = weights.numel()
         _check(table_build(self.handle, weights.data_ptr(), n, _dtype_code(weights), _stream_handle(stream)),
                "wrs_table_build")
@@ -352,7 +366,7 @@ class AliasTable:
 
     def build_psa_plus(self, weights, stream=None) -> "AliasTable":
         """PSA+ build (per-tile greedy pass, then PSA on the leftovers)."""
-        assert weights.is_cuda and weights.is_contiguous()
+        _require_cuda(weights, "weights")
         n = weights.numel()
         _check(table_build_psa_plus(self.handle, weights.data_ptr(), n, _dtype_code(weights),
                                     _stream_handle(stream)), "wrs_table_build_psa_plus")
@@ -369,7 +383,7 @@ class AliasTable:
 
         if out is None:
             out = torch.empty(k, dtype=torch.int32, device="cuda")
-        assert out.is_cuda and out.is_contiguous() and out.numel() >= k and out.element_size() == 4
+        _require_cuda(out, "out", k, 4)
         _check(sample(self.handle, k, seed, stream_id, out.data_ptr(), _stream_handle(stream)), "wrs_sample")
         return out
 
@@ -443,18 +457,20 @@ class AliasBatch:
         dtype = dtype or tensors[0].dtype
         buf = torch.zeros(self.offsets[-1], dtype=dtype, device="cuda")
         for t, x in enumerate(tensors):
-            assert x.numel() == self.sizes[t]
+            if x.numel() != self.sizes[t]:
+                raise ValueError(f"table {t} has {self.sizes[t]} weights, got {x.numel()}")
             buf[self.offsets[t]:self.offsets[t] + self.sizes[t]].copy_(x.reshape(-1))
         return buf
 
     def build(self, weights, stream=None) -> "AliasBatch":
-        assert weights.is_cuda and weights.is_contiguous() and weights.numel() >= self.offsets[-1]
+        _require_cuda(weights, "weights", self.offsets[-1])
         _check(batch_build(self.handle, weights.data_ptr(), _dtype_code(weights), _stream_handle(stream)),
                "wrs_batch_build")
         return self
 
     def set_samples(self, ks) -> list:
-        assert len(ks) == self.ntables
+        if len(ks) != self.ntables:
+            raise ValueError(f"{self.ntables} sample counts needed, got {len(ks)}")
         rc, self.k_offsets = batch_set_samples(self.handle, ks)
         _check(rc, "wrs_batch_set_samples")
         return self.k_offsets
@@ -465,7 +481,7 @@ class AliasBatch:
         total = self.k_offsets[-1] if self.k_offsets else 0
         if out is None:
             out = torch.empty(max(total, 1), dtype=torch.int32, device="cuda")
-        assert out.is_cuda and out.is_contiguous() and out.numel() >= total and out.element_size() == 4
+        _require_cuda(out, "out", total, 4)
         _check(batch_sample(self.handle, seed, stream_id, out.data_ptr(), _stream_handle(stream)),
                "wrs_batch_sample")
         return out
@@ -573,7 +589,7 @@ class AliasTable2:
         self.n = 0
 
     def build(self, weights, stream=None) -> "AliasTable2":
-        assert weights.is_cuda and weights.is_contiguous()
+        _require_cuda(weights, "weights")
         n = weights.numel()
         _check(table2_build(self.handle, weights.data_ptr(), n, _dtype_code(weights), _stream_handle(stream)),
                "wrs_table2_build")
@@ -585,7 +601,7 @@ class AliasTable2:
 
         if out is None:
             out = torch.empty(max(k, 1), dtype=torch.int32, device="cuda")
-        assert out.is_cuda and out.is_contiguous() and out.numel() >= k and out.element_size() == 4
+        _require_cuda(out, "out", k, 4)
         _check(table2_sample(self.handle, k, seed, stream_id, out.data_ptr(), _stream_handle(stream)),
                "wrs_table2_sample")
         return out
@@ -600,6 +616,7 @@ class AliasTable2:
         table was built from."""
         import torch
 
+        _require_cuda(weights, "weights", self.n)
         if capacity is None:
             capacity = min(k, self.n + 128 * (self.n // TABLE2_GROUP + 1)) + 1
         items = torch.empty(max(capacity, 1), dtype=torch.int32, device="cuda")

@@ -116,3 +116,48 @@ def test_every_entry_point_rejects_null_handles_without_a_gpu(wrs):
     assert lib.wrs_table2_layout(None, None, None) == E
     assert lib.wrs_table2_sample_os(None, None, 1, 10, 1, 0, None, None, 0, None, None) == E
     wrs.table2_free(None)
+
+
+def test_binding_refuses_what_the_kernels_must_not_see():
+    """Host tensors, strided views, short outputs and wrong element sizes are
+    refused before any launch (explicit checks that stay under python -O)."""
+    import torch
+
+    from paper_1903_00227_gb300 import wrs
+
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        wrs._require_cuda(torch.zeros(8), "weights")
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        wrs._require_cuda(torch.zeros(8, dtype=torch.int32), "out", 8, 4)
+    with pytest.raises(TypeError):
+        wrs._dtype_code(torch.zeros(4, dtype=torch.float64))
+
+
+class _DeviceLike:
+    """Stands in for a CUDA tensor's metadata (no device needed)."""
+
+    is_cuda = True
+
+    def __init__(self, numel, itemsize=4, contiguous=True):
+        self._n, self._s, self._c = numel, itemsize, contiguous
+
+    def is_contiguous(self):
+        return self._c
+
+    def numel(self):
+        return self._n
+
+    def element_size(self):
+        return self._s
+
+
+def test_binding_checks_layout_size_and_element_size():
+    from paper_1903_00227_gb300 import wrs
+
+    wrs._require_cuda(_DeviceLike(8), "out", 8, 4)  # accepted
+    with pytest.raises(ValueError, match="contiguous"):
+        wrs._require_cuda(_DeviceLike(8, contiguous=False), "weights")
+    with pytest.raises(ValueError, match="7 elements, 8 needed"):
+        wrs._require_cuda(_DeviceLike(7), "out", 8, 4)
+    with pytest.raises(ValueError, match="4-byte elements"):
+        wrs._require_cuda(_DeviceLike(8, itemsize=8), "out", 8, 4)
