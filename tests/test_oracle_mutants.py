@@ -12,6 +12,7 @@ from tests import test_oracle_2lvl as TL
 from tests import test_oracle_osnd as OS
 from tests import test_oracle_pins as P
 from tests import test_oracle_psaplus as PP
+from tests import test_oracle_sample_at as SA
 
 SRC = os.path.join(os.path.dirname(O.__file__), "wrs_oracle.c")
 
@@ -105,6 +106,37 @@ PP_MUTANTS = {
     "pp_next_heavy_is_light": ("                    while (jn < t1 && is_light(&in, jn)) ++jn;",
                                "                    while (jn < t1 && !is_light(&in, jn)) ++jn;"),
 }
+
+
+# The indexed queries (the checkers of the full-size sample tests), caught by
+# the pins of test_oracle_sample_at.py.
+SA_MUTANTS = {
+    # the sample index's high word dropped from the counter
+    "sample_at_counter_hi": ("        uint64_t s = s_idx[t];\n        uint32_t key[2], ctr[4], x[4];\n        uint64_t u, v, r;\n"
+                             "        key[0] = (uint32_t)seed; key[1] = (uint32_t)(seed >> 32);\n"
+                             "        ctr[0] = (uint32_t)s; ctr[1] = (uint32_t)(s >> 32);",
+                             "        uint64_t s = s_idx[t];\n        uint32_t key[2], ctr[4], x[4];\n        uint64_t u, v, r;\n"
+                             "        key[0] = (uint32_t)seed; key[1] = (uint32_t)(seed >> 32);\n"
+                             "        ctr[0] = (uint32_t)s; ctr[1] = 0;"),
+    # the seed's words swapped in the key
+    "sample_at_key_swapped": ("        uint64_t s = s_idx[t];\n        uint32_t key[2], ctr[4], x[4];\n        uint64_t u, v, r;\n"
+                              "        key[0] = (uint32_t)seed; key[1] = (uint32_t)(seed >> 32);",
+                              "        uint64_t s = s_idx[t];\n        uint32_t key[2], ctr[4], x[4];\n        uint64_t u, v, r;\n"
+                              "        key[0] = (uint32_t)(seed >> 32); key[1] = (uint32_t)seed;"),
+    # the listed position used as the counter instead of the listed sample index
+    "sample_at_position": ("        uint64_t s = s_idx[t];\n", "        uint64_t s = t;\n"),
+    # the two-level walk drops the sample index's high word
+    "sample_2lvl_counter_hi": ("        key[1] = (uint32_t)(seed >> 32) + (uint32_t)d * 0xBB67AE85u;\n"
+                               "        ctr[0] = (uint32_t)s; ctr[1] = (uint32_t)(s >> 32);",
+                               "        key[1] = (uint32_t)(seed >> 32) + (uint32_t)d * 0xBB67AE85u;\n"
+                               "        ctr[0] = (uint32_t)s; ctr[1] = 0;"),
+    # the indexed two-level queries walk sample t instead of the listed index
+    "sample_2lvl_at_position": ("out[t] = sample_2lvl_one(L, sizes, G, thr, al, qp, seed, stream, s_idx[t]);",
+                                "out[t] = sample_2lvl_one(L, sizes, G, thr, al, qp, seed, stream, t);"),
+}
+
+SA_PINS = [SA.test_sample_at_equals_sequential_queries, SA.test_sample_at_high_counter_words_against_published_philox,
+           SA.test_sample_2lvl_at_equals_sequential_walk, SA.test_sample_2lvl_at_bottom_level_against_published_philox]
 
 
 def _pp_alias_tables():
@@ -244,3 +276,9 @@ def test_every_planted_osnd_mistake_is_caught(name, tmp_path):
 def test_every_planted_mistake_is_caught(name, tmp_path):
     old, new = MUTANTS[name]
     assert _run_mutant(old, new, PINS, tmp_path), f"mutant {name} passed every pin"
+
+
+@pytest.mark.parametrize("name", sorted(SA_MUTANTS))
+def test_every_planted_indexed_query_mistake_is_caught(name, tmp_path):
+    old, new = SA_MUTANTS[name]
+    assert _run_mutant(old, new, SA_PINS, tmp_path), f"mutant {name} passed every indexed-query pin"
