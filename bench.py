@@ -21,10 +21,12 @@ copy bandwidth, with its DRAM traffic from the committed ncu summaries;
 workload.  The other rows ride on the same line: ``psa_plus`` (PSA+ builds),
 ``two_level`` (two-level tables, with ``os_nd`` output-sensitive sampling),
 ``many_tables`` (4096 tables built and sampled in one CUDA graph against one
-table at a time) and ``serving`` (a Poisson request stream against one
-request at a time; ``--serve-loads`` adds ``serving.load_sweep``, both paths
-at fractions of the plain path's saturation rate), each with the oracle timed
-beside it where it applies.
+table at a time), ``serving`` (a Poisson request stream against one request
+at a time, then ``serving.load_sweep``: both paths at 0.5, 0.8 and 0.95 of
+the plain path's saturation rate, ``--serve-loads``) and ``small_exact`` (n =
+10^6 u32 weights, k = 10^6: build and sample latency in microseconds, L2
+resident, checked bit for bit against the oracle), each with the oracle
+timed beside it where it applies.
 
 ``--impl reference`` times the CPU oracle itself (the reference arm of this
 repository) on bounded samples of the same workload.
@@ -85,9 +87,11 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=100_000,
                     help="requests of the serving workload (0: skip it)")
     ap.add_argument("--serve-rate", type=float, default=20_000.0, help="Poisson arrival rate, requests/s")
-    ap.add_argument("--serve-loads", default="",
+    ap.add_argument("--serve-loads", default="0.5,0.8,0.95",
                     help="comma-separated fractions of the plain path's saturation rate to offer in a load "
                          "sweep after the serving run (empty: no sweep)")
+    ap.add_argument("--no-small", action="store_true",
+                    help="skip the small exact configuration (n = 10^6 u32 weights, L2-resident latency)")
     ap.add_argument("--serve-sweep-requests", type=int, default=20_000, help="requests per load-sweep point")
     return ap.parse_args()
 
@@ -685,6 +689,50 @@ def run_serving(args, torch):
     return out
 
 
+def run_small(torch, WL, wrs, stream, reps: int = 50):
+    """The small exact configuration: n = 10^6 u32 weights uniform in [1, 2^24]
+    (seed 1), built as 64 split pieces (the table does not depend on the
+    split count), then k = 10^6 samples (seed 2, stream 0).  Table (4 MB of
+    weights, 16 MB of buckets) and samples stay in L2, so the figures are
+    latencies in microseconds (median of `reps` CUDA-event timings on the
+    launching stream), not an HBM claim.  The table and samples are checked
+    against the oracle once."""
+    from oracle import wrs_oracle as O
+    import numpy as np
+
+    n, k = 1_000_000, 1_000_000
+    w = WL.u32_uniform(n, 1)
+    w_dev = torch.from_numpy(w.view(np.int32).copy()).cuda()
+    out = torch.empty(k, dtype=torch.int32, device="cuda")
+    sh = stream.cuda_stream
+    tb, ts = [], []
+    with wrs.AliasTable(n) as t:
+        for i in range(reps + 3):
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            t.build(w_dev, stream=sh)
+            e1.record(stream)
+            t.sample(k, seed=2, stream_id=0, out=out, stream=sh)
+            e2.record(stream)
+            e2.synchronize()
+            if i >= 3:
+                tb.append(e0.elapsed_time(e1) * 1e3)
+                ts.append(e1.elapsed_time(e2) * 1e3)
+        if t.status() != wrs.OK:
+            raise RuntimeError("small configuration: build failed")
+        thr, alias, _ = t.download()
+    qz, tab = O.build_table(w)
+    want = O.sample(tab.thr, tab.alias, tab.Qp, k, 2, 0)
+    exact = bool(np.array_equal(thr, tab.thr) and np.array_equal(alias, tab.alias)
+                 and np.array_equal(out.cpu().numpy().view(np.uint32), want))
+    b_us, s_us = statistics.median(tb), statistics.median(ts)
+    return {"workload": "n=1e6 u32 weights uniform in [1, 2^24] (seed 1), 64 split pieces, k=1e6 samples "
+                        "(seed 2, stream 0)",
+            "build_us": b_us, "sample_us": s_us, "build_gweights_s": n / (b_us * 1e-6) / 1e9,
+            "sample_gsamples_s": k / (s_us * 1e-6) / 1e9, "reps": reps, "bit_exact_vs_oracle": exact,
+            "l2_resident": True, "note": "4 MB weights and 16 MB table fit in the 129 MB L2: latency, no HBM claim"}
+
+
 def run_e2e(args, torch, wrs, table, weights, names, stream, ws):
     """The step through the C ABI's host-buffer entry points, with every host
     <-> device copy inside the timed region: wrs_table_build_host uploads
@@ -909,6 +957,10 @@ def run_ours(args, names):
                   "sampler_fraction": gms / (t_sample / K),
                   "note": "random 16-B gathers from the same table with no RNG or coin: the random-access ceiling"}
 
+    small = None
+    if not args.no_small:
+        small = run_small(torch, WL, wrs, stream)
+
     # end to end through the C ABI with host buffers (copies inside the timed region)
     e2e = None
     if args.e2e_steps > 0:
@@ -958,7 +1010,8 @@ def run_ours(args, names):
                                "frac": ach_build / peak, "algorithmic_bytes_per_weight": BUILD_BYTES_PER_WEIGHT,
                                "peak_source": peak_kind},
             "kernels": per_kernel, "per_dist": per_dist,
-            "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "psa_plus": psa_plus, "two_level": two_level, "many_tables": batched, "serving": serving,
+            "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "psa_plus": psa_plus, "two_level": two_level,
+            "many_tables": batched, "serving": serving, "small_exact": small,
             "gpu_launches": K * (len(wrs.STAGES) + 1),
             "context": {"paper_psa_build_gweights_s_n1e9": 0.99, "paper_psa_query_gsamples_s_n1e9": 1.662,
                         "paper_hardware": "4x Xeon Gold 6138, 158 threads (context only)"},

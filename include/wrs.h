@@ -87,8 +87,11 @@ typedef struct {
 typedef struct wrs_table wrs_table; /* opaque; device memory owned by the library */
 
 /* Allocate a table (buckets and workspace) for up to capacity_n weights.
- * capacity_n in [1, 2^32 - 1].  Synchronous (cudaMalloc); the table can be
- * rebuilt any number of times.  Device memory: 16 B per bucket plus about
+ * capacity_n in [1, 2^32 - 1].  Synchronous (stream-ordered allocation on a
+ * stream of the table's own, waited for before returning); the table can be
+ * rebuilt any number of times.  Every later call on a table records CUDA
+ * events on the streams it is given, so that the host-side calls below wait
+ * for this table's work only.  Device memory: 16 B per bucket plus about
  * 0.09 B per weight of workspace.  Errors: WRS_EINVAL, WRS_ENOMEM. */
 wrs_status wrs_table_create(uint64_t capacity_n, wrs_table **out);
 
@@ -111,16 +114,16 @@ wrs_status wrs_table_build(wrs_table *t, const void *d_weights, uint64_t n,
  * differs from wrs_table_build's (the tiles pair items locally) but obeys the
  * same contract, and wrs_sample and every other table call accept it.
  * Arguments, ownership and errors as for wrs_table_build.  The first PSA+
- * build of a table allocates 40 B per weight of its capacity (synchronous
- * cudaMalloc), kept until wrs_table_free; later builds allocate nothing and
- * are asynchronous. */
+ * build of a table allocates 40 B per weight of its capacity (stream-ordered
+ * cudaMallocAsync on `stream`), kept until wrs_table_free; later builds
+ * allocate nothing.  Asynchronous. */
 wrs_status wrs_table_build_psa_plus(wrs_table *t, const void *d_weights, uint64_t n,
                                     wrs_dtype dtype, void *stream);
 
 /* Number of items the last build's tile phase left over (the length of the
  * list the second phase built), when that build was wrs_table_build_psa_plus.
- * Synchronises the device.  Errors: WRS_EINVAL (no PSA+ build is the table's
- * last), WRS_EDEVICE. */
+ * Waits for that build (as wrs_table_status).  Errors: WRS_EINVAL (no PSA+
+ * build is the table's last), WRS_EDEVICE. */
 wrs_status wrs_table_psa_plus_leftovers(const wrs_table *t, uint64_t *n_left);
 
 /* wrs_table_create(n) followed by wrs_table_build(). */
@@ -153,22 +156,28 @@ wrs_status wrs_table_build_host(wrs_table *t, const void *h_weights, uint64_t n,
 wrs_status wrs_sample_host(wrs_table *t, uint64_t k, uint64_t seed,
                            uint64_t stream_id, uint32_t *h_out, void *stream);
 
-/* Synchronise the device and return the status word of the last build. */
+/* Wait for the table's last build to complete (the host waits for that
+ * build's event only, not for the device or other tables' work) and return
+ * its status word. */
 wrs_status wrs_table_status(const wrs_table *t);
 
-/* Synchronise and fill *info (header of the last build). */
+/* Wait for the table's last build (as wrs_table_status) and fill *info
+ * (header of the last build). */
 wrs_status wrs_table_info_get(const wrs_table *t, wrs_table_info *info);
 
 /* Device pointer to the n buckets (wrs_bucket[n]) of the last build; owned
  * by the table, valid until the table is freed or rebuilt. */
 const wrs_bucket *wrs_table_buckets(const wrs_table *t);
 
-/* Synchronise and copy n buckets to h_buckets (bytes >= 16 n). */
+/* Wait for the table's last build (as wrs_table_status) and copy n buckets
+ * to h_buckets (bytes >= 16 n). */
 wrs_status wrs_table_download(const wrs_table *t, void *h_buckets, uint64_t bytes);
 
 /* Install buckets computed elsewhere (for testing the query on its own):
  * copies n buckets from host memory and sets Q, beta; shift and qp are
- * derived from Q as in a build.  Synchronous. */
+ * derived from Q as in a build.  Ordered after every earlier operation on
+ * the table, on a stream of the library's own; returns when the copy is
+ * complete. */
 wrs_status wrs_table_upload(wrs_table *t, const void *h_buckets, uint64_t n,
                             uint64_t q_lo, uint64_t q_hi, int32_t beta);
 
@@ -182,7 +191,10 @@ wrs_status wrs_table_upload(wrs_table *t, const void *h_buckets, uint64_t n,
 wrs_status wrs_table_set_timing(wrs_table *t, int enable);
 wrs_status wrs_table_stage_ms(const wrs_table *t, float *ms, uint32_t count);
 
-/* Free all memory of the table (synchronises the device first).  NULL ok. */
+/* Free the table.  Stream-ordered: the device memory is released once every
+ * operation enqueued on the table (builds and samples, on whichever streams
+ * the caller used) has completed; the call itself does not wait.  The
+ * caller must not enqueue further work on the table.  NULL ok. */
 void wrs_table_free(wrs_table *t);
 
 /* Static string for a status code. */
@@ -398,10 +410,10 @@ wrs_status wrs_table2_sample_os(wrs_table2 *t, const void *d_weights, wrs_dtype 
 /*
  * Build without allocating (no counterpart in the paper).
  *
- * For callers that cannot call cudaMalloc -- code running inside a CUDA graph
- * being captured or replayed, real-time or embedded processes whose memory is
- * fixed at start-up, host frameworks that own all device memory through their
- * own pool -- this entry point builds the same table as wrs_table_build
+ * For callers that cannot call cudaMalloc -- real-time or embedded processes
+ * whose device memory is fixed at start-up, host frameworks that own all
+ * device memory through their own pool and forbid allocations behind its
+ * back -- this entry point builds the same table as wrs_table_build
  * (bucket for bucket) into memory the caller owns, and keeps its scratch in
  * one static device array inside the library, sized for WRS_NOALLOC_MAX_N
  * weights (about 0.5 MB; every GPU that loads the library holds it until the
@@ -421,19 +433,25 @@ wrs_status wrs_table2_sample_os(wrs_table2 *t, const void *d_weights, wrs_dtype 
  * All calls share the one array: two calls whose work overlaps on the GPU
  * (different streams, or several host threads) race and corrupt each
  * other's results, so order them (one stream, or events).  The array keeps
- * the last call's contents; nothing in it needs to start at zero. */
+ * the last call's contents; the one part that must start at zero, the
+ * look-back flags, is cleared by each call on `stream` (cudaMemsetAsync,
+ * which allocates nothing) before the scan that reads them. */
 #define WRS_NOALLOC_MAX_N (1ull << 22)
 #define WRS_DEVICE_HEADER_BYTES 128
 
+/* Every field is written by every build; the caller only reads them.  The
+ * two fields marked "library" are working state of the build: their values
+ * after a build carry no meaning for the caller, and the caller must not
+ * store into them. */
 typedef struct {
     uint32_t status;      /* wrs_status of the build */
-    uint32_t reserved0;
+    uint32_t tile_counter; /* library: block ids of the look-back scan */
     int32_t beta;         /* exponent of the integer unit */
     uint32_t shift;       /* thr = bw >> shift */
     uint64_t q_lo, q_hi;  /* Q */
     uint64_t qp;          /* Q >> shift: the sampler's coin denominator */
     uint32_t light_max;   /* light iff raw word <= light_max */
-    uint32_t reserved1;
+    uint32_t f32;         /* library: 1 if the weights were binary32 words */
     uint64_t n;
     uint64_t n_light;
     uint64_t reserved2[8];

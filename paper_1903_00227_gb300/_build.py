@@ -24,7 +24,7 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared"
 EXTRA = {"libwrs.so": ["-fmad=false"]}
 
 TARGETS = {
-    "libwrs.so": (["wrs.cu"], ["wrs_device.cuh", "wrs_kernels.cuh", "wrs_batch.cuh", "wrs_twolevel.cuh", "wrs_osnd.cuh"], [os.path.join(INCLUDE, "wrs.h")]),
+    "libwrs.so": (["wrs.cu"], ["wrs_device.cuh", "wrs_kernels.cuh", "wrs_batch.cuh", "wrs_twolevel.cuh", "wrs_osnd.cuh", "wrs_psaplus.cuh"], [os.path.join(INCLUDE, "wrs.h")]),
     "libwrs_workloads.so": (["workloads.cu"], [], []),
 }
 

@@ -6,6 +6,7 @@
 #include <atomic>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "wrs.h"
@@ -14,6 +15,21 @@
 using namespace wrs;
 
 constexpr int kStages = 6; // stats, stats_combine, classify, tilescan, split, sweep
+constexpr int kOpSlots = 8; // streams whose last operation on a table is tracked
+
+// The last operation a table enqueued on each stream it was used with, and
+// the end of its last build: the waits of the host-side calls (status,
+// info, download, upload, free) wait for these events only, never for the
+// whole device.
+struct OpLog {
+    std::mutex mu;
+    cudaStream_t priv = nullptr;  // library-private stream: read-backs, uploads, frees
+    cudaEvent_t build_ev = nullptr;
+    bool built = false;
+    cudaStream_t slot_stream[kOpSlots] = {};
+    cudaEvent_t slot_ev[kOpSlots] = {};
+    int nslots = 0, next = 0;
+};
 
 struct wrs_table {
     uint64_t cap;          // capacity in weights
@@ -42,6 +58,7 @@ struct wrs_table {
     int timed_build;       // the last build recorded ev[]
     uint8_t *pp_ws;        // PSA+ scratch (allocated by the first PSA+ build)
     uint64_t pp_n;         // n of the last PSA+ build (0: the last build was not PSA+)
+    OpLog *log;            // per-stream completion events
 };
 
 namespace {
@@ -91,20 +108,85 @@ int sm_count()
     return sms > 0 ? sms : 1;
 }
 
-bool g_attr_done[64];
+std::atomic<bool> g_attr_done[64];
+std::mutex g_attr_mu;
 
 wrs_status set_kernel_attributes()
 {
     int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64) return WRS_EDEVICE;
-    if (g_attr_done[dev]) return WRS_OK;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return WRS_EDEVICE;
+    if (g_attr_done[dev].load(std::memory_order_acquire)) return WRS_OK;
+    std::lock_guard<std::mutex> lock(g_attr_mu);
+    if (g_attr_done[dev].load(std::memory_order_relaxed)) return WRS_OK;
     const int bytes = (int)sizeof(SweepSmem);
     cudaError_t e = cudaFuncSetAttribute(k_sweep<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sweep<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return WRS_EDEVICE;
-    g_attr_done[dev] = true;
+    g_attr_done[dev].store(true, std::memory_order_release);
     return WRS_OK;
+}
+
+// Record the end of an operation on table t enqueued on stream s (and of its
+// build, when it is one).  A stream beyond the tracked slots takes the slot
+// used longest ago, after the host has waited for that slot's operation.
+wrs_status log_op(wrs_table *t, cudaStream_t s, bool build)
+{
+    OpLog &L = *t->log;
+    std::lock_guard<std::mutex> lock(L.mu);
+    cudaError_t e = cudaSuccess;
+    if (build) {
+        e = cudaEventRecord(L.build_ev, s);
+        if (e != cudaSuccess) return cuda_err(e);
+        L.built = true;
+    }
+    int k = 0;
+    while (k < L.nslots && L.slot_stream[k] != s) ++k;
+    if (k == L.nslots) {
+        if (L.nslots < kOpSlots) {
+            e = cudaEventCreateWithFlags(&L.slot_ev[k], cudaEventDisableTiming);
+            if (e != cudaSuccess) return cuda_err(e);
+            ++L.nslots;
+        } else {
+            k = L.next;
+            L.next = (L.next + 1) % kOpSlots;
+            e = cudaEventSynchronize(L.slot_ev[k]);
+            if (e != cudaSuccess) return cuda_err(e);
+        }
+        L.slot_stream[k] = s;
+    }
+    return cuda_err(cudaEventRecord(L.slot_ev[k], s));
+}
+
+// Host wait for the table's last build only.
+wrs_status wait_build(const wrs_table *t)
+{
+    OpLog &L = *t->log;
+    std::lock_guard<std::mutex> lock(L.mu);
+    return L.built ? cuda_err(cudaEventSynchronize(L.build_ev)) : WRS_OK;
+}
+
+// Make the private stream wait for every tracked operation on the table
+// (device-side ordering; the host does not wait).
+wrs_status order_after_all(const wrs_table *t)
+{
+    OpLog &L = *t->log;
+    std::lock_guard<std::mutex> lock(L.mu);
+    for (int k = 0; k < L.nslots; ++k) {
+        cudaError_t e = cudaStreamWaitEvent(L.priv, L.slot_ev[k], 0);
+        if (e != cudaSuccess) return cuda_err(e);
+    }
+    return WRS_OK;
+}
+
+// Copy device bytes of the table to host memory after its last build, on
+// the private stream.
+wrs_status read_back(const wrs_table *t, void *h, const void *d, size_t bytes)
+{
+    wrs_status st = wait_build(t);
+    if (st != WRS_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(h, d, bytes, cudaMemcpyDeviceToHost, t->log->priv);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(t->log->priv);
+    return cuda_err(e);
 }
 
 wrs_status enqueue_build(wrs_table *t, const void *d_weights, uint64_t n, wrs_dtype dtype, cudaStream_t s)
@@ -154,6 +236,7 @@ wrs_status enqueue_build(wrs_table *t, const void *d_weights, uint64_t n, wrs_dt
     if (tm) cudaEventRecord(t->ev[6], s);
     t->timed_build = tm;
     wrs_status st = launch_err();
+    if (st == WRS_OK) st = log_op(t, s, true);
     if (st == WRS_OK) {
         t->n = n;
         t->host_status = -1;
@@ -178,10 +261,16 @@ wrs_status launch_sample(const wrs_table *t, uint64_t s0, uint64_t s1, uint64_t 
 
 wrs_status read_status(const wrs_table *t, uint32_t *out)
 {
-    cudaError_t e = cudaDeviceSynchronize();
-    if (e != cudaSuccess) return WRS_EDEVICE;
-    e = cudaMemcpy(out, &t->hdr->status, sizeof(uint32_t), cudaMemcpyDeviceToHost);
-    return cuda_err(e);
+    return read_back(t, out, &t->hdr->status, sizeof(uint32_t));
+}
+
+void destroy_log(OpLog *L)
+{
+    if (!L) return;
+    for (int k = 0; k < L->nslots; ++k) cudaEventDestroy(L->slot_ev[k]);
+    if (L->build_ev) cudaEventDestroy(L->build_ev);
+    if (L->priv) cudaStreamDestroy(L->priv); // pending work still completes
+    delete L;
 }
 
 } // namespace
@@ -196,15 +285,29 @@ wrs_status wrs_table_create(uint64_t capacity_n, wrs_table **out)
     wrs_table *t = new (std::nothrow) wrs_table();
     if (!t) return WRS_ENOMEM;
     std::memset(t, 0, sizeof(*t));
+    t->log = new (std::nothrow) OpLog();
+    if (!t->log) { delete t; return WRS_ENOMEM; }
     t->cap = capacity_n;
     t->ntiles_cap = (uint32_t)((capacity_n + kTile - 1) / kTile);
     t->host_status = -1;
     cudaGetDevice(&t->device);
     const Layout L = layout_for(t->ntiles_cap);
-    cudaError_t e = cudaMalloc(&t->ws, L.total);
-    if (e != cudaSuccess) { delete t; return cuda_err(e); }
-    e = cudaMalloc(&t->buckets, capacity_n * sizeof(uint4));
-    if (e != cudaSuccess) { cudaFree(t->ws); delete t; return cuda_err(e); }
+    cudaError_t e = cudaStreamCreateWithFlags(&t->log->priv, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t->log->build_ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) { destroy_log(t->log); delete t; return cuda_err(e); }
+    // stream-ordered allocations on the private stream, so that freeing the
+    // table is stream-ordered too (cudaFreeAsync)
+    cudaStream_t ps = t->log->priv;
+    e = cudaMallocAsync(reinterpret_cast<void **>(&t->ws), L.total, ps);
+    if (e != cudaSuccess) { destroy_log(t->log); delete t; return cuda_err(e); }
+    e = cudaMallocAsync(reinterpret_cast<void **>(&t->buckets), capacity_n * sizeof(uint4), ps);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(t->ws, ps);
+        cudaStreamSynchronize(ps);
+        destroy_log(t->log);
+        delete t;
+        return cuda_err(e);
+    }
     t->hdr = reinterpret_cast<DevHeader *>(t->ws + L.hdr);
     t->part = reinterpret_cast<Partial *>(t->ws + L.part);
     t->agg = reinterpret_cast<TileSum *>(t->ws + L.agg);
@@ -214,9 +317,16 @@ wrs_status wrs_table_create(uint64_t capacity_n, wrs_table **out)
     t->flags = reinterpret_cast<uint32_t *>(t->ws + L.flags);
     t->split = reinterpret_cast<Split *>(t->ws + L.split);
     t->slist = reinterpret_cast<uint16_t *>(t->ws + L.slist);
-    e = cudaMemset(t->ws, 0, L.total);
-    if (e == cudaSuccess) e = cudaDeviceSynchronize();
-    if (e != cudaSuccess) { cudaFree(t->ws); cudaFree(t->buckets); delete t; return cuda_err(e); }
+    e = cudaMemsetAsync(t->ws, 0, L.total, ps);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ps);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(t->ws, ps);
+        cudaFreeAsync(t->buckets, ps);
+        cudaStreamSynchronize(ps);
+        destroy_log(t->log);
+        delete t;
+        return cuda_err(e);
+    }
     *out = t;
     return WRS_OK;
 }
@@ -249,7 +359,10 @@ wrs_status wrs_sample(const wrs_table *t, uint64_t k, uint64_t seed, uint64_t st
     if (k == 0) return WRS_OK;
     if (!d_out) return WRS_EINVAL;
     if (t->host_status > 0) return (wrs_status)t->host_status;
-    return launch_sample(t, 0, k, seed, stream_id, d_out, static_cast<cudaStream_t>(stream));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    wrs_status st = launch_sample(t, 0, k, seed, stream_id, d_out, s);
+    if (st == WRS_OK) st = log_op(const_cast<wrs_table *>(t), s, false);
+    return st;
 }
 
 wrs_status wrs_table_build_host(wrs_table *t, const void *h_weights, uint64_t n, wrs_dtype dtype, void *stream)
@@ -257,13 +370,19 @@ wrs_status wrs_table_build_host(wrs_table *t, const void *h_weights, uint64_t n,
     if (!t || !h_weights || n == 0 || n > t->cap) return WRS_EINVAL;
     if (dtype != WRS_U32 && dtype != WRS_F32) return WRS_EINVAL;
     const uint64_t bytes = n * 4;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (t->stage_w_bytes < bytes) {
-        if (t->stage_w) { cudaDeviceSynchronize(); cudaFree(t->stage_w); t->stage_w = nullptr; t->stage_w_bytes = 0; }
-        cudaError_t e = cudaMalloc(&t->stage_w, bytes);
+        if (t->stage_w) { // freed once every operation of the table that may read it is done
+            wrs_status st = order_after_all(t);
+            if (st != WRS_OK) return st;
+            cudaFreeAsync(t->stage_w, t->log->priv);
+            t->stage_w = nullptr;
+            t->stage_w_bytes = 0;
+        }
+        cudaError_t e = cudaMallocAsync(&t->stage_w, bytes, s);
         if (e != cudaSuccess) return cuda_err(e);
         t->stage_w_bytes = bytes;
     }
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemcpyAsync(t->stage_w, h_weights, bytes, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_err(e);
     return enqueue_build(t, t->stage_w, n, dtype, s);
@@ -276,9 +395,14 @@ wrs_status wrs_sample_host(wrs_table *t, uint64_t k, uint64_t seed, uint64_t str
     if (k == 0) return WRS_OK;
     if (!h_out) return WRS_EINVAL;
     if (t->host_status > 0) return (wrs_status)t->host_status;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (t->stage_out_cap < k) {
-        if (t->stage_out) { cudaDeviceSynchronize(); cudaFree(t->stage_out); t->stage_out = nullptr; t->stage_out_cap = 0; }
-        cudaError_t e = cudaMalloc(&t->stage_out, k * sizeof(uint32_t));
+        if (t->stage_out) { // every earlier host-buffer sample has synchronised already
+            cudaFreeAsync(t->stage_out, s);
+            t->stage_out = nullptr;
+            t->stage_out_cap = 0;
+        }
+        cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&t->stage_out), k * sizeof(uint32_t), s);
         if (e != cudaSuccess) return cuda_err(e);
         t->stage_out_cap = k;
     }
@@ -289,7 +413,6 @@ wrs_status wrs_sample_host(wrs_table *t, uint64_t k, uint64_t seed, uint64_t str
     }
     // sample in chunks; each chunk's copy to the host runs on copy_stream
     // while the next chunk is drawn
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     const uint64_t chunk = 1ull << 25;
     for (uint64_t c0 = 0; c0 < k; c0 += chunk) {
         const uint64_t c1 = c0 + chunk < k ? c0 + chunk : k;
@@ -302,6 +425,8 @@ wrs_status wrs_sample_host(wrs_table *t, uint64_t k, uint64_t seed, uint64_t str
                                 t->copy_stream);
         if (e != cudaSuccess) return cuda_err(e);
     }
+    wrs_status st = log_op(t, s, false);
+    if (st != WRS_OK) return st;
     cudaError_t e = cudaStreamSynchronize(t->copy_stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     return cuda_err(e);
@@ -322,11 +447,9 @@ wrs_status wrs_table_info_get(const wrs_table *t, wrs_table_info *info)
 {
     if (!t || !info) return WRS_EINVAL;
     if (t->n == 0) return WRS_EINVAL;
-    cudaError_t e = cudaDeviceSynchronize();
-    if (e != cudaSuccess) return WRS_EDEVICE;
     DevHeader h;
-    e = cudaMemcpy(&h, t->hdr, sizeof(h), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return WRS_EDEVICE;
+    const wrs_status st = read_back(t, &h, t->hdr, sizeof(h));
+    if (st != WRS_OK) return st;
     info->n = t->n;
     info->q_lo = h.q_lo;
     info->q_hi = h.q_hi;
@@ -348,9 +471,7 @@ const wrs_bucket *wrs_table_buckets(const wrs_table *t)
 wrs_status wrs_table_download(const wrs_table *t, void *h_buckets, uint64_t bytes)
 {
     if (!t || !h_buckets || t->n == 0 || bytes < t->n * sizeof(uint4)) return WRS_EINVAL;
-    cudaError_t e = cudaDeviceSynchronize();
-    if (e == cudaSuccess) e = cudaMemcpy(h_buckets, t->buckets, t->n * sizeof(uint4), cudaMemcpyDeviceToHost);
-    return cuda_err(e);
+    return read_back(t, h_buckets, t->buckets, t->n * sizeof(uint4));
 }
 
 wrs_status wrs_table_upload(wrs_table *t, const void *h_buckets, uint64_t n, uint64_t q_lo, uint64_t q_hi,
@@ -371,10 +492,17 @@ wrs_status wrs_table_upload(wrs_table *t, const void *h_buckets, uint64_t n, uin
     h.q_hi = q_hi;
     h.qp = (uint64_t)(Q >> shift);
     h.n = n;
-    cudaError_t e = cudaDeviceSynchronize();
-    if (e == cudaSuccess) e = cudaMemcpy(t->buckets, h_buckets, n * sizeof(uint4), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(t->hdr, &h, sizeof(h), cudaMemcpyHostToDevice);
+    // after every operation of the table (samples may still read the
+    // buckets), on the private stream; synchronous for the caller
+    wrs_status st = order_after_all(t);
+    if (st != WRS_OK) return st;
+    cudaStream_t ps = t->log->priv;
+    cudaError_t e = cudaMemcpyAsync(t->buckets, h_buckets, n * sizeof(uint4), cudaMemcpyHostToDevice, ps);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(t->hdr, &h, sizeof(h), cudaMemcpyHostToDevice, ps);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ps);
     if (e != cudaSuccess) return cuda_err(e);
+    st = log_op(t, ps, true);
+    if (st != WRS_OK) return st;
     t->n = n;
     t->host_status = 0;
     t->pp_n = 0;
@@ -394,8 +522,7 @@ wrs_status wrs_table_set_timing(wrs_table *t, int enable)
         }
         t->timing = 1;
     } else if (!enable && t->timing) {
-        cudaDeviceSynchronize();
-        for (int i = 0; i <= kStages; ++i) cudaEventDestroy(t->ev[i]);
+        for (int i = 0; i <= kStages; ++i) cudaEventDestroy(t->ev[i]); // pending records still complete
         t->timing = 0;
         t->timed_build = 0;
     }
@@ -414,16 +541,23 @@ wrs_status wrs_table_stage_ms(const wrs_table *t, float *ms, uint32_t count)
 void wrs_table_free(wrs_table *t)
 {
     if (!t) return;
-    cudaDeviceSynchronize();
+    // stream-ordered: the memory is released on the private stream once every
+    // tracked operation of the table has completed; the host does not wait
+    const wrs_status st = order_after_all(t);
+    cudaStream_t ps = t->log->priv;
+    if (st != WRS_OK) cudaStreamSynchronize(ps);
     if (t->timing)
         for (int i = 0; i <= kStages; ++i) cudaEventDestroy(t->ev[i]);
-    cudaFree(t->ws);
-    cudaFree(t->buckets);
-    if (t->stage_w) cudaFree(t->stage_w);
-    if (t->stage_out) cudaFree(t->stage_out);
+    if (t->copy_ev) cudaEventRecord(t->copy_ev, t->copy_stream);
+    if (t->copy_ev) cudaStreamWaitEvent(ps, t->copy_ev, 0);
+    cudaFreeAsync(t->ws, ps);
+    cudaFreeAsync(t->buckets, ps);
+    if (t->stage_w) cudaFreeAsync(t->stage_w, ps);
+    if (t->stage_out) cudaFreeAsync(t->stage_out, ps);
+    if (t->pp_ws) cudaFreeAsync(t->pp_ws, ps);
     if (t->copy_stream) cudaStreamDestroy(t->copy_stream);
     if (t->copy_ev) cudaEventDestroy(t->copy_ev);
-    if (t->pp_ws) cudaFree(t->pp_ws);
+    destroy_log(t->log);
     delete t;
 }
 
@@ -457,10 +591,10 @@ void wrs_debug_skip_publish(int64_t tile)
 // ---------------------------------------------------------------------------
 // Build without any allocation (wrs_build_noalloc).
 //
-// Some callers cannot call cudaMalloc: code that runs inside a CUDA graph
-// being captured or replayed, a real-time or embedded process whose memory
-// budget is fixed at start-up, or a host framework that owns all device
-// memory through its own pool.  For them, the build's scratch (per-block
+// Some callers cannot call cudaMalloc: a real-time or embedded process whose
+// device memory budget is fixed at start-up, or a host framework that owns
+// all device memory through its own pool and forbids allocations behind its
+// back.  For them, the build's scratch (per-block
 // partial sums, tile sums and prefixes, look-back flags, split results,
 // sparse member lists) lives in one file-scope device array sized for
 // WRS_NOALLOC_MAX_N weights; the caller passes the weights, the output
@@ -483,19 +617,23 @@ constexpr uint64_t kNaSplit = kNaFlags + na_up((uint64_t)kNaChunks * sizeof(uint
 constexpr uint64_t kNaSlist = kNaSplit + na_up((uint64_t)kNaTiles * sizeof(Split));
 constexpr uint64_t kNaBytes = kNaSlist + na_up((uint64_t)kNaTiles * kSparse * sizeof(uint16_t));
 
-// Zero at module load; the look-back flags carry a generation number, so no
-// call has to clear them.
+// Zero at module load.  Every call clears the look-back flags on its stream
+// before the scan and publishes with generation 1, so nothing on the launch
+// path depends on host state that changes from call to call.
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 
+constexpr uint32_t kNaEpoch = 1;
+
 struct NoallocDevice {
-    unsigned char *scratch; // device address of g_noalloc_scratch on this device
-    uint32_t epoch;
-    bool ready;
+    std::atomic<unsigned char *> scratch{nullptr}; // device address of g_noalloc_scratch on this device
+    std::mutex init;                               // first-call set-up, once per device
 };
 NoallocDevice g_noalloc[64];
 
 static_assert(sizeof(DevHeader) <= WRS_DEVICE_HEADER_BYTES, "device header does not fit");
 static_assert(offsetof(DevHeader, status) == offsetof(wrs_device_header, status), "layout");
+static_assert(offsetof(DevHeader, tile_counter) == offsetof(wrs_device_header, tile_counter), "layout");
+static_assert(offsetof(DevHeader, f32) == offsetof(wrs_device_header, f32), "layout");
 static_assert(offsetof(DevHeader, beta) == offsetof(wrs_device_header, beta), "layout");
 static_assert(offsetof(DevHeader, shift) == offsetof(wrs_device_header, shift), "layout");
 static_assert(offsetof(DevHeader, q_lo) == offsetof(wrs_device_header, q_lo), "layout");
@@ -520,15 +658,19 @@ extern "C" wrs_status wrs_build_noalloc(const void *d_weights, uint64_t n, wrs_d
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return WRS_EDEVICE;
     NoallocDevice &D = g_noalloc[dev];
-    if (!D.ready) {
+    unsigned char *scratch = D.scratch.load(std::memory_order_acquire);
+    if (!scratch) {
         // once per device, with that device current: the array's device address
-        void *ptr = nullptr;
-        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return WRS_EDEVICE;
-        const wrs_status st = set_kernel_attributes();
-        if (st != WRS_OK) return st;
-        D.scratch = static_cast<unsigned char *>(ptr);
-        D.epoch = 0;
-        D.ready = true;
+        std::lock_guard<std::mutex> lock(D.init);
+        scratch = D.scratch.load(std::memory_order_relaxed);
+        if (!scratch) {
+            void *ptr = nullptr;
+            if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return WRS_EDEVICE;
+            const wrs_status st = set_kernel_attributes();
+            if (st != WRS_OK) return st;
+            scratch = static_cast<unsigned char *>(ptr);
+            D.scratch.store(scratch, std::memory_order_release);
+        }
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const uint32_t *w = static_cast<const uint32_t *>(d_weights);
@@ -538,29 +680,30 @@ extern "C" wrs_status wrs_build_noalloc(const void *d_weights, uint64_t n, wrs_d
     const uint32_t f32 = dtype == WRS_F32;
     DevHeader *hdr = static_cast<DevHeader *>(d_header);
     uint4 *buckets = static_cast<uint4 *>(d_buckets);
-    Partial *part = reinterpret_cast<Partial *>(D.scratch + kNaPart);
-    TileSum *agg = reinterpret_cast<TileSum *>(D.scratch + kNaAgg);
-    TileSum *incl = reinterpret_cast<TileSum *>(D.scratch + kNaIncl);
-    TileSum *cagg = reinterpret_cast<TileSum *>(D.scratch + kNaCagg);
-    TileSum *cincl = reinterpret_cast<TileSum *>(D.scratch + kNaCincl);
-    uint32_t *flags = reinterpret_cast<uint32_t *>(D.scratch + kNaFlags);
-    Split *split = reinterpret_cast<Split *>(D.scratch + kNaSplit);
-    uint16_t *slist = reinterpret_cast<uint16_t *>(D.scratch + kNaSlist);
+    Partial *part = reinterpret_cast<Partial *>(scratch + kNaPart);
+    TileSum *agg = reinterpret_cast<TileSum *>(scratch + kNaAgg);
+    TileSum *incl = reinterpret_cast<TileSum *>(scratch + kNaIncl);
+    TileSum *cagg = reinterpret_cast<TileSum *>(scratch + kNaCagg);
+    TileSum *cincl = reinterpret_cast<TileSum *>(scratch + kNaCincl);
+    uint32_t *flags = reinterpret_cast<uint32_t *>(scratch + kNaFlags);
+    Split *split = reinterpret_cast<Split *>(scratch + kNaSplit);
+    uint16_t *slist = reinterpret_cast<uint16_t *>(scratch + kNaSlist);
 
     uint64_t want = (n + (uint64_t)kThreads * 16 - 1) / ((uint64_t)kThreads * 16);
     uint32_t nparts = (uint32_t)(want < 1 ? 1 : (want > kMaxParts ? kMaxParts : want));
     const uint32_t blocks_cap = (uint32_t)sm_count() * 8;
     if (nparts > blocks_cap) nparts = blocks_cap;
     uint32_t cls_blocks = blocks_cap < ntiles ? blocks_cap : ntiles;
-    D.epoch = D.epoch + 1;
-    if (D.epoch >= (1u << 30)) D.epoch = 1;
+    // the look-back flags start from zero on the stream, in stream order with
+    // the scan that reads them
+    if (cudaMemsetAsync(flags, 0, (size_t)nchunks * sizeof(uint32_t), s) != cudaSuccess) return WRS_EDEVICE;
 
     if (f32) k_stats<1><<<nparts, kThreads, 0, s>>>(w, n, vec, part);
     else k_stats<0><<<nparts, kThreads, 0, s>>>(w, n, vec, part);
     k_stats_combine<<<1, kThreads, 0, s>>>(part, nparts, n, f32, hdr);
     if (f32) k_classify<1><<<cls_blocks, kThreads, 0, s>>>(w, n, vec, hdr, agg, slist, ntiles);
     else k_classify<0><<<cls_blocks, kThreads, 0, s>>>(w, n, vec, hdr, agg, slist, ntiles);
-    k_tilescan<<<nchunks, kThreads, 0, s>>>(hdr, agg, cagg, cincl, incl, flags, ntiles, D.epoch,
+    k_tilescan<<<nchunks, kThreads, 0, s>>>(hdr, agg, cagg, cincl, incl, flags, ntiles, kNaEpoch,
                                             g_wait_limit.load(), kNone);
     k_split<<<(ntiles + kThreads - 1) / kThreads, kThreads, 0, s>>>(incl, ntiles, n, hdr, split);
     const uint32_t sweep_blocks = (ntiles + kSweepTiles - 1) / kSweepTiles;

@@ -566,7 +566,8 @@ wrs_status wrs_table_build_psa_plus(wrs_table *t, const void *d_weights, uint64_
     if (st != WRS_OK) return st;
     const PpLayout L = pp_layout(t->cap);
     if (!t->pp_ws) {
-        cudaError_t e = cudaMalloc(&t->pp_ws, L.total);
+        cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&t->pp_ws), L.total,
+                                        static_cast<cudaStream_t>(stream));
         if (e != cudaSuccess) {
             t->pp_ws = nullptr;
             return cuda_err(e);
@@ -612,6 +613,7 @@ wrs_status wrs_table_build_psa_plus(wrs_table *t, const void *d_weights, uint64_
     k_pp_starts<<<(nmerge + kWarps - 1) / kWarps, kThreads, 0, s>>>(keys, t->hdr, tot, starts);
     k_pp_merge<<<nmerge, kThreads, sizeof(PpSmem), s>>>(keys, kidx, t->hdr, tot, starts, t->buckets);
     st = launch_err();
+    if (st == WRS_OK) st = log_op(t, s, true);
     if (st == WRS_OK) {
         t->n = n;
         t->host_status = -1;
@@ -626,9 +628,8 @@ wrs_status wrs_table_psa_plus_leftovers(const wrs_table *t, uint64_t *n_left)
     if (!t || !n_left || !t->pp_ws || t->pp_n == 0 || t->pp_n != t->n) return WRS_EINVAL;
     const PpLayout L = pp_layout(t->cap);
     uint32_t m = 0;
-    cudaError_t e = cudaDeviceSynchronize();
-    if (e == cudaSuccess) e = cudaMemcpy(&m, t->pp_ws + L.m, sizeof(m), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return cuda_err(e);
+    const wrs_status st = read_back(t, &m, t->pp_ws + L.m, sizeof(m));
+    if (st != WRS_OK) return st;
     *n_left = m;
     return WRS_OK;
 }

@@ -1,6 +1,6 @@
 """wrs_build_noalloc: the build for callers that cannot allocate device
-memory (graph capture, fixed-budget real-time processes, frameworks that own
-all device memory).  It must produce, through the C ABI, exactly the buckets
+memory (real-time processes with a device memory budget fixed at start-up,
+frameworks that own all device memory through their own pool).  It must produce, through the C ABI, exactly the buckets
 and header values of the ordinary build, call after call, although every call
 reuses the library's one static scratch array.  This file is collected last
 so that a failure here comes after every other test has run."""
