@@ -212,8 +212,8 @@ wrs_status enqueue_build(wrs_table *t, const void *d_weights, uint64_t n, wrs_dt
     const uint32_t skip_tile = skip < 0 ? kNone : (uint32_t)skip;
 
     const uint32_t nchunks = (ntiles + kScanChunk - 1) / kScanChunk;
-    uint32_t cls_blocks = (uint32_t)sm_count() * 8;
-    if (cls_blocks > ntiles) cls_blocks = ntiles;
+    uint32_t cls_blocks = (uint32_t)sm_count() * 8; // one warp per tile
+    if (cls_blocks > (ntiles + kWarps - 1) / kWarps) cls_blocks = (ntiles + kWarps - 1) / kWarps;
     const bool tm = t->timing != 0;
     if (tm) cudaEventRecord(t->ev[0], s);
     if (f32) k_stats<1><<<nparts, kThreads, 0, s>>>(w, n, vec, t->part);
@@ -693,7 +693,8 @@ extern "C" wrs_status wrs_build_noalloc(const void *d_weights, uint64_t n, wrs_d
     uint32_t nparts = (uint32_t)(want < 1 ? 1 : (want > kMaxParts ? kMaxParts : want));
     const uint32_t blocks_cap = (uint32_t)sm_count() * 8;
     if (nparts > blocks_cap) nparts = blocks_cap;
-    uint32_t cls_blocks = blocks_cap < ntiles ? blocks_cap : ntiles;
+    const uint32_t cls_want = (ntiles + kWarps - 1) / kWarps; // one warp per tile
+    uint32_t cls_blocks = blocks_cap < cls_want ? blocks_cap : cls_want;
     // the look-back flags start from zero on the stream, in stream order with
     // the scan that reads them
     if (cudaMemsetAsync(flags, 0, (size_t)nchunks * sizeof(uint32_t), s) != cudaSuccess) return WRS_EDEVICE;

@@ -71,10 +71,10 @@ __global__ void __launch_bounds__(kThreads) kb_classify(const uint32_t *__restri
                                                         const BlockMap *__restrict__ map, const DevHeader *hdr,
                                                         TileSum *__restrict__ agg, uint16_t *__restrict__ slist)
 {
-    const BlockMap m = map[blockIdx.x];
+    const BlockMap m = map[blockIdx.x]; // block m.local: tiles 8 m.local .. 8 m.local + 7, one per warp
     const BatchTable &T = bt[m.table];
     classify_body<F32>(w + T.off, T.n, vec, hdr + m.table, agg + T.tile0, slist + (uint64_t)T.tile0 * kSparse,
-                       T.ntiles, m.local, T.ntiles);
+                       T.ntiles, m.local * kWarps + (threadIdx.x >> 5), T.ntiles);
 }
 
 __global__ void __launch_bounds__(kThreads) kb_tilescan(const BatchTable *__restrict__ bt,
@@ -387,7 +387,7 @@ wrs_status wrs_batch_create(uint32_t ntables, const uint64_t *h_n, wrs_batch **o
     for (uint32_t t = 0; t < ntables; ++t) {
         const BatchTable &T = b->h[t];
         for (uint32_t i = 0; i < T.nparts; ++i) ms.push_back(BlockMap{t, i});
-        for (uint32_t i = 0; i < T.ntiles; ++i) mc.push_back(BlockMap{t, i});
+        for (uint32_t i = 0; i < (T.ntiles + kWarps - 1) / kWarps; ++i) mc.push_back(BlockMap{t, i});
         for (uint32_t i = 0; i < (T.ntiles + kScanChunk - 1) / kScanChunk; ++i) mscan.push_back(BlockMap{t, i});
         for (uint32_t i = 0; i < (T.ntiles + kThreads - 1) / kThreads; ++i) msplit.push_back(BlockMap{t, i});
     }

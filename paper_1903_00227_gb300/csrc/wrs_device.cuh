@@ -14,6 +14,8 @@ constexpr int kThreads = 256;               // threads per block of the build
 constexpr int kItems = 8;                   // weights per thread
 constexpr int kTile = kThreads * kItems;    // weights per tile (2048)
 constexpr int kWarps = kThreads / 32;
+constexpr int kChunk = 32 * kItems;         // weights of one warp's share of a tile (256)
+constexpr int kChunks = kTile / kChunk;     // chunks per tile (8)
 constexpr int kSparse = 32;                 // member lists of tiles with <= 32 heavies (or lights)
 constexpr int kScanChunk = kThreads;        // tile aggregates per block of the look-back scan
 constexpr uint32_t kNone = 0xFFFFFFFFu;

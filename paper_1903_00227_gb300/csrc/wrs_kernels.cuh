@@ -168,8 +168,33 @@ __device__ Acc acc_block_reduce(Acc a)
     return a; // valid in thread 0
 }
 
+// Add the exact value S * 2^(e0 - 150) of a chunk, whose lowest set bit is
+// at 2^(e0 - 150 + ctz(o)), to an accumulator kept in units of 2^base (base:
+// the lowest set bit seen so far).
+__device__ __forceinline__ void acc_add_chunk(Acc &a, uint64_t S, uint64_t o, int e0)
+{
+    const int lsb = e0 - 150 + __ffsll((long long)o) - 1;
+    if (lsb < a.base) { // a lower set bit than any before: rebase
+        if (a.acc) {
+            const int d = a.base - lsb;
+            if (bitlen128(a.acc) + d > kQBits) { a.flags |= kPartOverflow; a.acc = 0; }
+            else a.acc <<= d;
+        }
+        a.base = lsb;
+    }
+    const int sh = e0 - 150 - a.base; // >= -ctz(o), and S is a multiple of 2^ctz(o)
+    a.acc += sh >= 0 ? ((u128)S << sh) : (u128)(S >> (-sh));
+    if (hi64(a.acc) >> (kQBits - 64)) { a.flags |= kPartOverflow; a.acc = 0; }
+}
+
 // Block `bid` of `nblk` blocks sharing the weights of one table; thread 0
-// writes the block's partial to *out.
+// writes the block's partial to *out.  Binary32 weights go in warp chunks
+// of 256 (lane l: weights 8l .. 8l+7): when every weight of a chunk is a
+// normal number and their exponents span at most 31 binades, the chunk's
+// exact sum is formed in 64 bits as sum m * 2^(e - e0) (e0: the chunk's
+// smallest exponent; one multiply-add per weight, below 2^63 over the warp)
+// and its lowest set bit from the OR of those terms; any other chunk takes
+// the exact per-weight path.
 template <int F32>
 __device__ __forceinline__ void stats_body(const uint32_t *__restrict__ w, uint64_t n, int vec, uint32_t bid,
                                            uint32_t nblk, Partial *__restrict__ out)
@@ -179,30 +204,89 @@ __device__ __forceinline__ void stats_body(const uint32_t *__restrict__ w, uint6
     a.acc = 0;
     a.flags = 0;
     uint64_t a64 = 0;
-    const uint64_t tid = (uint64_t)bid * kThreads + threadIdx.x;
-    const uint64_t nth = (uint64_t)nblk * kThreads;
-    const uint64_t nv = vec ? n / 4 : 0;
-    const uint4 *w4 = reinterpret_cast<const uint4 *>(w);
-    uint64_t i = tid;
-    for (; i + 3 * nth < nv; i += 4 * nth) {
-        const uint4 v0 = __ldg(w4 + i), v1 = __ldg(w4 + i + nth), v2 = __ldg(w4 + i + 2 * nth), v3 = __ldg(w4 + i + 3 * nth);
-        acc_take<F32>(a, a64, v0.x); acc_take<F32>(a, a64, v0.y); acc_take<F32>(a, a64, v0.z); acc_take<F32>(a, a64, v0.w);
-        acc_take<F32>(a, a64, v1.x); acc_take<F32>(a, a64, v1.y); acc_take<F32>(a, a64, v1.z); acc_take<F32>(a, a64, v1.w);
-        if (F32) acc_fold(a, a64);
-        acc_take<F32>(a, a64, v2.x); acc_take<F32>(a, a64, v2.y); acc_take<F32>(a, a64, v2.z); acc_take<F32>(a, a64, v2.w);
-        acc_take<F32>(a, a64, v3.x); acc_take<F32>(a, a64, v3.y); acc_take<F32>(a, a64, v3.z); acc_take<F32>(a, a64, v3.w);
-        if (F32) acc_fold(a, a64);
+    if (!F32) {
+        const uint64_t tid = (uint64_t)bid * kThreads + threadIdx.x;
+        const uint64_t nth = (uint64_t)nblk * kThreads;
+        const uint64_t nv = vec ? n / 4 : 0;
+        const uint4 *w4 = reinterpret_cast<const uint4 *>(w);
+        uint64_t i = tid;
+        for (; i + 3 * nth < nv; i += 4 * nth) {
+            const uint4 v0 = __ldg(w4 + i), v1 = __ldg(w4 + i + nth), v2 = __ldg(w4 + i + 2 * nth), v3 = __ldg(w4 + i + 3 * nth);
+            a64 += (uint64_t)v0.x + v0.y + v0.z + v0.w;
+            a64 += (uint64_t)v1.x + v1.y + v1.z + v1.w;
+            a64 += (uint64_t)v2.x + v2.y + v2.z + v2.w;
+            a64 += (uint64_t)v3.x + v3.y + v3.z + v3.w;
+        }
+        for (; i < nv; i += nth) {
+            const uint4 v = __ldg(w4 + i);
+            a64 += (uint64_t)v.x + v.y + v.z + v.w;
+        }
+        for (uint64_t j = nv * 4 + tid; j < n; j += nth) a64 += __ldg(w + j);
+        acc_fold(a, a64); // n < 2^32 words below 2^32: the total fits 64 bits
+    } else {
+        const uint32_t lane = threadIdx.x & 31;
+        const uint64_t nchunks = (n + kChunk - 1) / kChunk;
+        const uint64_t cw = (uint64_t)nblk * kWarps;
+        Acc f; // the fast chunks' sum (the same in every lane)
+        f.base = INT_MAX; f.acc = 0; f.flags = 0;
+        uint32_t vmax = 0; // any word >= 0x7F800000 is Inf, NaN or has the sign bit set
+        uint64_t c = (uint64_t)bid * kWarps + (threadIdx.x >> 5);
+        uint32_t x[kItems];
+        if (c < nchunks) load_items(w, n, vec, c * kChunk + lane * kItems, x);
+        for (; c < nchunks; c += cw) {
+            const uint64_t first = c * kChunk + lane * kItems;
+            uint32_t xn[kItems];
+            const bool more = c + cw < nchunks;
+            if (more) load_items(w, n, vec, (c + cw) * kChunk + lane * kItems, xn);
+            bool fast = (c + 1) * kChunk <= n; // a full chunk (the same in every lane)
+            uint32_t e0 = 0;
+            if (fast) {
+                uint32_t emin = 0xFFFFFFFFu, emax = 0;
+#pragma unroll
+                for (int k = 0; k < kItems; ++k) {
+                    vmax = max(vmax, x[k]);
+                    const uint32_t ex = x[k] >> 23; // >= 255 for Inf, NaN and negative words
+                    emin = min(emin, ex);
+                    emax = max(emax, ex);
+                }
+                e0 = __reduce_min_sync(0xFFFFFFFFu, emin);
+                const uint32_t e1 = __reduce_max_sync(0xFFFFFFFFu, emax);
+                fast = e0 >= 1 && e1 < 255 && e1 - e0 <= 31; // all normal, finite, 31 binades
+            }
+            if (fast) {
+                uint64_t sum = 0, orr = 0;
+#pragma unroll
+                for (int k = 0; k < kItems; ++k) {
+                    const uint32_t m = (x[k] & 0x7FFFFFu) | 0x800000u;
+                    const uint64_t v = (uint64_t)m * (1u << ((x[k] >> 23) - e0)); // < 2^55
+                    sum += v;
+                    orr |= v;
+                }
+                // warp sum (< 2^63) by 16-bit limbs, warp OR by halves
+                uint64_t S = 0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    S += (uint64_t)__reduce_add_sync(0xFFFFFFFFu, (uint32_t)(sum >> (16 * q)) & 0xFFFFu) << (16 * q);
+                const uint64_t O = (uint64_t)__reduce_or_sync(0xFFFFFFFFu, (uint32_t)orr) |
+                                   ((uint64_t)__reduce_or_sync(0xFFFFFFFFu, (uint32_t)(orr >> 32)) << 32);
+                acc_add_chunk(f, S, O, (int)e0);
+            } else {
+#pragma unroll
+                for (int k = 0; k < kItems; ++k) {
+                    if (first + k < n) {
+                        acc_take<1>(a, a64, x[k]);
+                        acc_fold(a, a64);
+                    }
+                }
+            }
+            if (more) {
+#pragma unroll
+                for (int k = 0; k < kItems; ++k) x[k] = xn[k];
+            }
+        }
+        if (vmax >= 0x7F800000u) a.flags |= kPartInvalid;
+        if (lane == 0) acc_merge(a, f);
     }
-    for (; i < nv; i += nth) {
-        const uint4 v = __ldg(w4 + i);
-        acc_take<F32>(a, a64, v.x); acc_take<F32>(a, a64, v.y); acc_take<F32>(a, a64, v.z); acc_take<F32>(a, a64, v.w);
-        if (F32) acc_fold(a, a64);
-    }
-    for (uint64_t j = nv * 4 + tid; j < n; j += nth) {
-        acc_take<F32>(a, a64, __ldg(w + j));
-        if (F32) acc_fold(a, a64);
-    }
-    acc_fold(a, a64);
     a = acc_block_reduce(a);
     if (threadIdx.x == 0) {
         Partial p;
@@ -302,10 +386,6 @@ __device__ __forceinline__ uint64_t q64_of(uint32_t x, uint32_t f32, int beta)
     return sh >= 0 ? ((uint64_t)m << sh) : (uint64_t)(m >> (-sh));
 }
 
-// One 2048-weight tile per iteration of a grid-stride loop (no dependency
-// between tiles): light count, light and heavy sums, the tile's heavy count
-// and first heavy offset, and -- when one class has at most 32 members in the
-// tile -- the offsets of those members.
 __device__ __forceinline__ void tilesum_st(TileSum *p, const TileSum &v)
 {
     uint4 *d = reinterpret_cast<uint4 *>(p);
@@ -343,100 +423,113 @@ __device__ __forceinline__ u128 warp_sum128(u128 v)
     return r;
 }
 
-// Tiles t_first, t_first + t_stride, ... of one table.
+// Exclusive scan of a u32 over the warp.
+__device__ __forceinline__ uint32_t warp_excl_scan_u32(uint32_t v)
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t s = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, s, d);
+        if (lane >= d) s += o;
+    }
+    return s - v;
+}
+
+// Tiles t_first, t_first + t_stride, ... of one table, ONE WARP per tile
+// (no block barrier per tile).  A tile is eight chunks of 256 weights; lane
+// l holds weights 8l .. 8l+7 of a chunk.  Per tile: light count, light and
+// heavy sums of q, heavy count, offset of the first heavy, and the offsets of
+// its heavies when it has at most 32 of them.
 template <int F32>
 __device__ __forceinline__ void classify_body(const uint32_t *__restrict__ w, uint64_t n, int vec,
                                               const DevHeader *__restrict__ hdr, TileSum *__restrict__ agg,
                                               uint16_t *__restrict__ slist, uint32_t ntiles, uint32_t t_first,
                                               uint32_t t_stride)
 {
-    __shared__ u128 s_l[kWarps], s_h[kWarps];
-    __shared__ uint32_t s_c[kWarps], s_first[kWarps];
-    __shared__ uint32_t s_cnt[kWarps];
+    __shared__ uint16_t s_list[kWarps][kSparse];
     if (block_stopped(hdr)) return;
     const uint32_t light_max = hdr->light_max;
     const int beta = hdr->beta;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    uint32_t t = t_first;
+    const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint16_t *list = s_list[wid];
     uint32_t x[kItems];
-    if (t < ntiles) load_items(w, n, vec, (uint64_t)t * kTile + (uint64_t)threadIdx.x * kItems, x);
-    for (; t < ntiles; t += t_stride) {
-        const uint64_t first = (uint64_t)t * kTile + (uint64_t)threadIdx.x * kItems;
-        uint32_t cl = 0, nh = 0, fh = kNone, lm = 0;
-        // exact sums: 64-bit when every addend is below 2^61, else 128-bit
-        bool narrow = true;
-#pragma unroll
-        for (int k = 0; k < kItems; ++k) {
-            const bool valid = first + k < n;
-            if (valid && x[k] <= light_max) { ++cl; lm |= 1u << k; }
-            else if (valid) { ++nh; if (fh == kNone) fh = threadIdx.x * kItems + k; }
-            if (F32 && valid) {
-                const uint32_t ex = (x[k] >> 23) & 0xFFu;
-                if ((ex ? (int)ex : 1) - 150 - beta > 37) narrow = false;
-            }
-        }
-        u128 L, H;
-        if (narrow) {
-            uint64_t l64 = 0, h64 = 0;
+    if (t_first < ntiles) load_items(w, n, vec, (uint64_t)t_first * kTile + lane * kItems, x);
+    for (uint32_t t = t_first; t < ntiles; t += t_stride) {
+        const uint64_t tile0 = (uint64_t)t * kTile;
+        u128 Lp = 0, Hp = 0; // sums over the chunks so far (the same in every lane)
+        uint32_t clp = 0, chp = 0, fh = kNone;
+#pragma unroll 1
+        for (uint32_t c = 0; c < (uint32_t)kChunks; ++c) {
+            const uint64_t first = tile0 + c * kChunk + lane * kItems;
+            uint32_t lm = 0, hm = 0;
+            bool narrow = true;
 #pragma unroll
             for (int k = 0; k < kItems; ++k) {
                 if (first + k < n) {
+                    if (x[k] <= light_max) lm |= 1u << k; else hm |= 1u << k;
+                    if (F32) {
+                        const uint32_t ex = (x[k] >> 23) & 0xFFu;
+                        if ((ex ? (int)ex : 1) - 150 - beta > 37) narrow = false;
+                    }
+                }
+            }
+            u128 L = 0, H = 0;
+            if (__all_sync(0xFFFFFFFFu, narrow)) { // every q below 2^61: eight of them fit 64 bits
+                uint64_t l64 = 0, h64 = 0;
+#pragma unroll
+                for (int k = 0; k < kItems; ++k) {
                     const uint64_t q = q64_of(x[k], F32, beta);
-                    if ((lm >> k) & 1u) l64 += q; else h64 += q;
+                    if ((lm >> k) & 1u) l64 += q;
+                    if ((hm >> k) & 1u) h64 += q;
                 }
-            }
-            L = l64; H = h64;
-        } else {
-            L = 0; H = 0;
+                L = l64; H = h64;
+            } else {
 #pragma unroll
-            for (int k = 0; k < kItems; ++k) {
-                if (first + k < n) {
-                    const u128 q = q_of(x[k], F32, beta);
-                    if ((lm >> k) & 1u) L += q; else H += q;
+                for (int k = 0; k < kItems; ++k) {
+                    if (((lm | hm) >> k) & 1u) {
+                        const u128 q = q_of(x[k], F32, beta);
+                        if ((lm >> k) & 1u) L += q; else H += q;
+                    }
                 }
             }
+            // prefetch the next chunk (or the next tile's first) while reducing
+            const uint64_t nf = c + 1 < (uint32_t)kChunks ? first + kChunk
+                                                          : (uint64_t)(t + t_stride) * kTile + lane * kItems;
+            const bool more = c + 1 < (uint32_t)kChunks || t + t_stride < ntiles;
+            const uint32_t cl = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)__popc(lm));
+            const uint32_t ch = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)__popc(hm));
+            const uint32_t hb = __ballot_sync(0xFFFFFFFFu, hm != 0);
+            if (fh == kNone && hb) {
+                const int src = __ffs(hb) - 1;
+                const uint32_t hs = __shfl_sync(0xFFFFFFFFu, hm, src);
+                fh = c * kChunk + (uint32_t)src * kItems + (uint32_t)(__ffs(hs) - 1);
+            }
+            if (chp < (uint32_t)kSparse && hb) { // offsets of the first heavies, in order
+                uint32_t pos = chp + warp_excl_scan_u32((uint32_t)__popc(hm));
+#pragma unroll
+                for (int k = 0; k < kItems; ++k) {
+                    if ((hm >> k) & 1u) {
+                        if (pos < (uint32_t)kSparse) list[pos] = (uint16_t)(c * kChunk + lane * kItems + k);
+                        ++pos;
+                    }
+                }
+            }
+            if (more) load_items(w, n, vec, nf, x);
+            L = warp_sum128(L);
+            H = warp_sum128(H);
+            Lp += L; Hp += H;
+            clp += cl; chp += ch;
         }
-        const uint32_t lm_keep = lm;
-        const uint32_t cl_keep = cl, nh_keep = nh;
-        // prefetch the next tile of this block
-        const uint32_t tn = t + t_stride;
-        if (tn < ntiles) load_items(w, n, vec, (uint64_t)tn * kTile + (uint64_t)threadIdx.x * kItems, x);
-        // block reduction of (L, H, counts, first heavy)
-        const uint32_t cc = __reduce_add_sync(0xFFFFFFFFu, cl | (nh << 16)); // <= 256 per field
-        const uint32_t f = __reduce_min_sync(0xFFFFFFFFu, fh);
-        L = warp_sum128(L);
-        H = warp_sum128(H);
-        if (lane == 0) { s_l[wid] = L; s_h[wid] = H; s_c[wid] = cc; s_first[wid] = f; }
-        __syncthreads();
-        uint32_t ctot = 0;
-#pragma unroll
-        for (int i = 0; i < kWarps; ++i) ctot += s_c[i];
-        const uint32_t tot_l = ctot & 0xFFFFu, tot_h = ctot >> 16;
-        if (threadIdx.x == 0) {
-            u128 lt = 0, ht = 0;
+        __syncwarp();
+        if (lane == 0) {
             TileSum a;
-            a.first_heavy = kNone;
-#pragma unroll
-            for (int i = 0; i < kWarps; ++i) { lt += s_l[i]; ht += s_h[i]; a.first_heavy = min(a.first_heavy, s_first[i]); }
-            a.l_lo = lo64(lt); a.l_hi = hi64(lt); a.h_lo = lo64(ht); a.h_hi = hi64(ht);
-            a.cl = tot_l; a.nheavy = tot_h; a.pad = 0;
+            a.l_lo = lo64(Lp); a.l_hi = hi64(Lp); a.h_lo = lo64(Hp); a.h_hi = hi64(Hp);
+            a.cl = clp; a.nheavy = chp; a.first_heavy = fh; a.pad = 0;
             tilesum_st(agg + t, a);
         }
-        // member list of a sparse class (heavies first)
-        const bool list_heavy = tot_h <= (uint32_t)kSparse;
-        const bool list_light = !list_heavy && tot_l <= (uint32_t)kSparse;
-        if (list_heavy || list_light) {
-            uint32_t ctot2;
-            uint32_t slot = block_exclusive_scan_u32(list_heavy ? nh_keep : cl_keep, ctot2, s_cnt);
-#pragma unroll
-            for (int k = 0; k < kItems; ++k) {
-                if (first + k < n && (((lm_keep >> k) & 1u) != 0) == list_light) {
-                    slist[(uint64_t)t * kSparse + slot] = (uint16_t)(threadIdx.x * kItems + k);
-                    ++slot;
-                }
-            }
-        }
-        __syncthreads();
+        if (chp <= (uint32_t)kSparse && lane < chp) slist[(uint64_t)t * kSparse + lane] = list[lane];
+        __syncwarp();
     }
 }
 
@@ -445,7 +538,8 @@ __global__ void __launch_bounds__(kThreads) k_classify(const uint32_t *__restric
                                                        const DevHeader *__restrict__ hdr, TileSum *__restrict__ agg,
                                                        uint16_t *__restrict__ slist, uint32_t ntiles)
 {
-    classify_body<F32>(w, n, vec, hdr, agg, slist, ntiles, blockIdx.x, gridDim.x);
+    classify_body<F32>(w, n, vec, hdr, agg, slist, ntiles, blockIdx.x * kWarps + (threadIdx.x >> 5),
+                       gridDim.x * kWarps);
 }
 
 // ---------------------------------------------------------- k_tilescan
