@@ -215,6 +215,8 @@ typedef struct {
     u128 *L, *H;
 } wo_lists;
 
+typedef struct wo_psa_ctx wo_psa_ctx;
+
 static int split_pred(const wo_lists *s, uint64_t np, uint64_t j)
 {
     u128 sigma = s->L[np - j] + s->H[j];
@@ -245,70 +247,131 @@ static int wo_split(const wo_lists *s, uint64_t np, uint64_t *ri, uint64_t *rj, 
     return WO_OK;
 }
 
-/* splits (optional, 4 words per k = 0..p): n'_k, i_k, j_k, r_k low word */
-int wo_psa(uint64_t n, const uint64_t *q, const uint64_t *Qin, uint64_t p,
-           uint64_t *bw, uint32_t *al, uint64_t *splits)
-{
-    wo_in in = { n, q, ld128(Qin) };
+/* The steps of Alg. 3 as separate calls, so that a driver can run the     */
+/* p - 1 splits and the p packs (independent of each other, as the paper    */
+/* runs them on p PEs) concurrently: begin (the two traversals and their    */
+/* prefix sums), split(k) for 0 < k < p, pack(k) for 0 < k <= p once splits */
+/* k - 1 and k exist, end (canonicalise, split records, free).  wo_psa runs */
+/* them in order.                                                           */
+struct wo_psa_ctx {
+    wo_in in;
     wo_lists s;
-    uint64_t k, x, *si = NULL, *sj = NULL, *snp = NULL;
-    u128 *sr = NULL;
-    int rc = WO_OK;
-    if (p == 0 || p > n) return WO_EINVAL;
-    memset(&s, 0, sizeof s);
-    s.in = &in;
-    s.l = malloc(n * sizeof *s.l); s.h = malloc(n * sizeof *s.h);
-    s.L = malloc((n + 1) * sizeof *s.L); s.H = malloc((n + 1) * sizeof *s.H);
-    si = malloc((p + 1) * sizeof *si); sj = malloc((p + 1) * sizeof *sj);
-    snp = malloc((p + 1) * sizeof *snp); sr = malloc((p + 1) * sizeof *sr);
-    if (!s.l || !s.h || !s.L || !s.H || !si || !sj || !snp || !sr) { rc = WO_EINVAL; goto out; }
+    uint64_t p;
+    uint64_t *si, *sj, *snp;
+    u128 *sr;
+    uint64_t *bw;
+    uint32_t *al;
+};
 
-    /* the two parallel traversals of Alg. 3, plus prefix sums of their weights */
-    s.L[0] = 0; s.H[0] = 0;
-    for (x = 0; x < n; ++x) {
-        u128 qx = ld128(q + 2 * x);
-        if (is_light(&in, x)) { s.l[s.nl] = (uint32_t)x; s.L[s.nl + 1] = s.L[s.nl] + qx; ++s.nl; }
-        else                  { s.h[s.nh] = (uint32_t)x; s.H[s.nh + 1] = s.H[s.nh] + qx; ++s.nh; }
+void wo_psa_free(wo_psa_ctx *c)
+{
+    if (!c) return;
+    free(c->s.l); free(c->s.h); free(c->s.L); free(c->s.H);
+    free(c->si); free(c->sj); free(c->snp); free(c->sr);
+    free(c);
+}
+
+wo_psa_ctx *wo_psa_begin(uint64_t n, const uint64_t *q, const uint64_t *Qin, uint64_t p, uint64_t *bw, uint32_t *al)
+{
+    wo_psa_ctx *c;
+    uint64_t x;
+    if (p == 0 || p > n) return NULL;
+    c = calloc(1, sizeof *c);
+    if (!c) return NULL;
+    c->in.n = n; c->in.q = q; c->in.Q = ld128(Qin);
+    c->s.in = &c->in;
+    c->p = p; c->bw = bw; c->al = al;
+    c->s.l = malloc(n * sizeof *c->s.l); c->s.h = malloc(n * sizeof *c->s.h);
+    c->s.L = malloc((n + 1) * sizeof *c->s.L); c->s.H = malloc((n + 1) * sizeof *c->s.H);
+    c->si = malloc((p + 1) * sizeof *c->si); c->sj = malloc((p + 1) * sizeof *c->sj);
+    c->snp = malloc((p + 1) * sizeof *c->snp); c->sr = malloc((p + 1) * sizeof *c->sr);
+    if (!c->s.l || !c->s.h || !c->s.L || !c->s.H || !c->si || !c->sj || !c->snp || !c->sr) {
+        wo_psa_free(c);
+        return NULL;
     }
-
+    {
+        wo_in in = c->in;
+        wo_lists s = c->s;
+        /* the two parallel traversals of Alg. 3, plus prefix sums of their weights */
+        s.L[0] = 0; s.H[0] = 0;
+        for (x = 0; x < n; ++x) {
+            u128 qx = ld128(q + 2 * x);
+            if (is_light(&in, x)) { s.l[s.nl] = (uint32_t)x; s.L[s.nl + 1] = s.L[s.nl] + qx; ++s.nl; }
+            else                  { s.h[s.nh] = (uint32_t)x; s.H[s.nh + 1] = s.H[s.nh] + qx; ++s.nh; }
+        }
+        c->s.nl = s.nl; c->s.nh = s.nh;
+    }
     /* boundaries: k = 0 starts with the first heavy item whole; k = p is the end */
-    snp[0] = 0; si[0] = 0; sj[0] = 0; sr[0] = s.nh ? nq(&in, s.h[0]) : 0;
-    for (k = 1; k < p; ++k) {
-        snp[k] = (uint64_t)(((u128)n * k + p - 1) / p); /* ceil(n*k/p) */
-        rc = wo_split(&s, snp[k], &si[k], &sj[k], &sr[k]);
-        if (rc) goto out;
-    }
-    snp[p] = n; si[p] = s.nl; sj[p] = s.nh; sr[p] = 0;
+    c->snp[0] = 0; c->si[0] = 0; c->sj[0] = 0; c->sr[0] = c->s.nh ? nq(&c->in, c->s.h[0]) : 0;
+    c->snp[p] = n; c->si[p] = c->s.nl; c->sj[p] = c->s.nh; c->sr[p] = 0;
+    return c;
+}
 
-    for (k = 1; k <= p; ++k) { /* pack(k) */
-        uint64_t i = si[k - 1], j = sj[k - 1], step;
-        u128 r = sr[k - 1];
-        for (step = snp[k - 1]; step < snp[k]; ++step) {
+int wo_psa_split(wo_psa_ctx *c, uint64_t k)
+{
+    uint64_t n = c->in.n, p = c->p, *snp = c->snp;
+    if (k == 0 || k >= p) return WO_EINVAL;
+        snp[k] = (uint64_t)(((u128)n * k + p - 1) / p); /* ceil(n*k/p) */
+    return wo_split(&c->s, snp[k], &c->si[k], &c->sj[k], &c->sr[k]);
+}
+
+int wo_psa_pack(wo_psa_ctx *c, uint64_t k)
+{
+    wo_in in = c->in;
+    wo_lists s = c->s;
+    uint64_t *bw = c->bw;
+    uint32_t *al = c->al;
+    uint64_t i, j, step;
+    u128 r;
+    if (k == 0 || k > c->p) return WO_EINVAL;
+    s.in = &in;
+    i = c->si[k - 1]; j = c->sj[k - 1]; r = c->sr[k - 1];
+    for (step = c->snp[k - 1]; step < c->snp[k]; ++step) {
             if (j < s.nh && r <= in.Q) { /* heavy bucket h[j] */
                 uint64_t jn = j + 1;
                 put(bw, al, s.h[j], r, jn < s.nh ? s.h[jn] : s.h[j]);
                 if (jn < s.nh) r = (r + nq(&in, s.h[jn])) - in.Q;
-                else { if (r != in.Q) { rc = WO_EINTERNAL; goto out; } r = 0; }
+                else { if (r != in.Q) return WO_EINTERNAL; r = 0; }
                 j = jn;
             } else { /* light bucket l[i] */
-                if (i >= s.nl) { rc = WO_EINTERNAL; goto out; }
+                if (i >= s.nl) return WO_EINTERNAL;
                 put(bw, al, s.l[i], nq(&in, s.l[i]), j < s.nh ? s.h[j] : s.l[i]);
                 if (j < s.nh) r = (r + nq(&in, s.l[i])) - in.Q;
-                else if (nq(&in, s.l[i]) != in.Q) { rc = WO_EINTERNAL; goto out; }
+                else if (nq(&in, s.l[i]) != in.Q) return WO_EINTERNAL;
                 ++i;
             }
-        }
-        if (i != si[k] || j != sj[k] || (j < s.nh && r != sr[k])) { rc = WO_EINTERNAL; goto out; }
     }
-    canonicalise(n, in.Q, bw, al);
+    if (i != c->si[k] || j != c->sj[k] || (j < s.nh && r != c->sr[k])) return WO_EINTERNAL;
+    return WO_OK;
+}
+
+/* splits (optional, 4 words per k = 0..p): n'_k, i_k, j_k, r_k low word */
+void wo_psa_end(wo_psa_ctx *c, uint64_t *splits)
+{
+    uint64_t k;
+    canonicalise(c->in.n, c->in.Q, c->bw, c->al);
     if (splits)
-        for (k = 0; k <= p; ++k) {
-            splits[4 * k + 0] = snp[k]; splits[4 * k + 1] = si[k];
-            splits[4 * k + 2] = sj[k]; splits[4 * k + 3] = (uint64_t)sr[k];
+        for (k = 0; k <= c->p; ++k) {
+            splits[4 * k + 0] = c->snp[k]; splits[4 * k + 1] = c->si[k];
+            splits[4 * k + 2] = c->sj[k]; splits[4 * k + 3] = (uint64_t)c->sr[k];
         }
-out:
-    free(s.l); free(s.h); free(s.L); free(s.H); free(si); free(sj); free(snp); free(sr);
-    return rc;
+    wo_psa_free(c);
+}
+
+int wo_psa(uint64_t n, const uint64_t *q, const uint64_t *Qin, uint64_t p,
+           uint64_t *bw, uint32_t *al, uint64_t *splits)
+{
+    uint64_t k;
+    int rc = WO_OK;
+    wo_psa_ctx *c;
+    if (p == 0 || p > n) return WO_EINVAL;
+    c = wo_psa_begin(n, q, Qin, p, bw, al);
+    if (!c) return WO_EINVAL;
+    for (k = 1; k < p && rc == WO_OK; ++k) rc = wo_psa_split(c, k);
+    for (k = 1; k <= p && rc == WO_OK; ++k) rc = wo_psa_pack(c, k);
+    if (rc) { wo_psa_free(c); return rc; }
+    wo_psa_end(c, splits);
+    return WO_OK;
 }
 
 /* ------------------------------------------------------------------------ */

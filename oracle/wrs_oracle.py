@@ -103,6 +103,15 @@ def lib():
             L.wo_det_ldexp.restype = ctypes.c_double
             L.wo_psa_plus.argtypes = [U64, P, P, U64, P, P, P]
             L.wo_psa_plus.restype = INT
+            L.wo_psa_begin.argtypes = [U64, P, P, U64, P, P]
+            L.wo_psa_begin.restype = P
+            for f in (L.wo_psa_split, L.wo_psa_pack):
+                f.argtypes = [P, U64]
+                f.restype = INT
+            L.wo_psa_end.argtypes = [P, P]
+            L.wo_psa_end.restype = None
+            L.wo_psa_free.argtypes = [P]
+            L.wo_psa_free.restype = None
             _lib = L
     return _lib
 
@@ -252,6 +261,49 @@ def psa(qz: Quantized, p: int, return_splits: bool = False):
         raise OracleError(rc, "psa")
     t = Table(bw, al, qz.Qw)
     return (t, splits) if return_splits else t
+
+
+def psa_threads(qz: Quantized, p: int, threads: int, timings: dict | None = None) -> Table:
+    """Alg. 3 with its p - 1 splits and p packs run on `threads` host
+    threads (the oracle's own split and pack steps, unchanged; each call
+    releases the interpreter lock).  The table equals psa(qz, p)'s.  When
+    `timings` is a dict it receives the seconds of each phase."""
+    import time
+    from concurrent.futures import ThreadPoolExecutor
+
+    n = qz.n
+    L = lib()
+    bw = np.zeros((n, 2), dtype=np.uint64)
+    al = np.zeros(n, dtype=np.uint32)
+    t0 = time.perf_counter()
+    ctx = L.wo_psa_begin(n, _ptr(qz.q), _ptr(qz.Qw), p, _ptr(bw), _ptr(al))
+    if not ctx:
+        raise OracleError(1, "psa_begin")
+    t1 = time.perf_counter()
+    try:
+        def run(fn, ks):
+            rcs = [fn(ctx, k) for k in ks]
+            bad = [rc for rc in rcs if rc]
+            return bad[0] if bad else 0
+
+        with ThreadPoolExecutor(max_workers=threads) as ex:
+            parts = lambda lo, hi: [range(lo + i, hi, threads) for i in range(threads)]
+            rc = max(ex.map(lambda ks: run(L.wo_psa_split, ks), parts(1, p)), default=0)
+            t2 = time.perf_counter()
+            if rc == 0:
+                rc = max(ex.map(lambda ks: run(L.wo_psa_pack, ks), parts(1, p + 1)), default=0)
+        t3 = time.perf_counter()
+    except BaseException:
+        L.wo_psa_free(ctx)
+        raise
+    if rc:
+        L.wo_psa_free(ctx)
+        raise OracleError(rc, "psa_threads")
+    L.wo_psa_end(ctx, None)
+    t4 = time.perf_counter()
+    if timings is not None:
+        timings.update({"begin_s": t1 - t0, "splits_s": t2 - t1, "packs_s": t3 - t2, "end_s": t4 - t3})
+    return Table(bw, al, qz.Qw)
 
 
 def vose_f64(w: np.ndarray):
