@@ -332,6 +332,37 @@ def cpu_rows(names, n_s: int, batch_tables: int):
     return res
 
 
+def cpu_psa_all_cores(names, n_s: int):
+    """The oracle's exact PSA (Alg. 3) with P = host threads subproblems, its
+    P - 1 splits and P packs run on P host threads (the oracle's own split
+    and pack steps; ctypes releases the interpreter lock), on the same bounded
+    sample; quantisation and the two traversals with their prefix sums run on
+    one thread, as the oracle writes them."""
+    from oracle import wrs_oracle as O
+    from paper_1903_00227_gb300 import workloads as WL
+
+    nt = max(1, os.cpu_count() or 1)
+    tq = tt = 0.0
+    nw = 0
+    phases = {"begin_s": 0.0, "splits_s": 0.0, "packs_s": 0.0, "end_s": 0.0}
+    for name in names:
+        kind, s, seed = DISTS[name]
+        w = WL.generate(kind, n_s, seed, s)
+        t0 = time.perf_counter()
+        qz = O.quantize(w)
+        t1 = time.perf_counter()
+        ph = {}
+        O.psa_threads(qz, nt, nt, ph)
+        t2 = time.perf_counter()
+        tq += t1 - t0
+        tt += t2 - t1
+        nw += n_s
+        for key in phases:
+            phases[key] += ph[key]
+    return {"psa_all_cores_gweights_s": nw / (tq + tt) / 1e9, "psa_all_cores_threads": nt,
+            "psa_all_cores_phase_s": {"quantize_s": tq, **phases}}
+
+
 def cpu_sample_all_cores(n_s: int):
     """The oracle's sampler on every host core: threads draw disjoint ranges
     of sample indices with the oracle's indexed query (ctypes releases the
@@ -362,6 +393,7 @@ def cpu_baseline(names, n_s: int):
            "sample": f"first {n_s:,} weights of each of {', '.join(names)} (same recipes), "
                      f"exact quantize + Alg. 2 sweep, then {n_s:,} queries each; single thread"}
     out.update(cpu_other_builders(names, n_s))
+    out.update(cpu_psa_all_cores(names, n_s))
     out.update(cpu_sample_all_cores(n_s))
     out["cpu_model"] = cpu_model()
     out["host_threads"] = os.cpu_count()
@@ -633,8 +665,13 @@ def run_batched(args, torch, WL, wrs, stream):
                     f"uniform (0,1] or Zipf 1.0 by seed, k log-uniform in [1, 4096] (total {total_k})",
         "batched": {"ms_per_step": bms, "p99_ms": srt[min(len(srt) - 1, int(round(0.99 * (len(srt) - 1))))],
                     "gweights_s": total_w / (bms * 1e-3) / 1e9, "tables_per_s": len(n) / (bms * 1e-3),
-                    "launches_per_step": 8, "cuda_graph": True, "tuned_groups": groups,
-                    "tuned_sweep_ms": tuned_ms, "tune_seconds": tune_s},
+                    "launches_per_step": 8 + (1 if any(x <= 2048 for x in n) else 0), "cuda_graph": True,
+                    "tuned_groups": groups, "tuned_sweep_ms": tuned_ms, "tune_seconds": tune_s,
+                    "one_block_tables": sum(1 for x in n if x <= 2048),
+                    "roofline_build": {"algorithmic_bytes": 24 * total_w,
+                                       "frac": 24 * total_w / (bms * 1e-3) / 1e9 / measured_peaks()[0],
+                                       "note": "24 B/weight over all tables' weights against the measured copy "
+                                               "bandwidth; the step also draws the samples"}},
         "plain": {"ms_per_step": pms, "gweights_s": total_w / (pms * 1e-3) / 1e9,
                   "tables_per_s": len(n) / (pms * 1e-3),
                   "launches_per_step": 7 * len(n) + sum(1 for x in k if x),

@@ -713,7 +713,7 @@ extern "C" wrs_status wrs_build_noalloc(const void *d_weights, uint64_t n, wrs_d
     return launch_err();
 }
 
-#include "wrs_batch.cuh"
 #include "wrs_twolevel.cuh"
+#include "wrs_batch.cuh"
 #include "wrs_osnd.cuh"
 #include "wrs_psaplus.cuh"

@@ -5,7 +5,10 @@
 // Every stage of the build is one launch over all tables: a block looks up
 // (table, block within the table) in a per-stage map and runs the same body
 // as the single-table kernel on that table's slice of the concatenated
-// arrays.  Tables never read each other's data, so table t's buckets and
+// arrays.  Tables of at most one tile (2048 weights) skip those stages: one
+// block builds each of them whole in shared memory (kb_small: total, exact
+// units, light threshold and Alg. 2 in the table's own units, which for a
+// single group are the units of the whole table).  Tables never read each other's data, so table t's buckets and
 // samples are exactly those of a single-table build of its weights (and of
 // wrs_sample with stream id stream_id + t).  Nothing on the launch path reads
 // a host value that changes between builds -- the look-back generation lives
@@ -52,6 +55,7 @@ __global__ void __launch_bounds__(kThreads) kb_stats(const uint32_t *__restrict_
 }
 
 // One block per table; block 0 also advances the look-back generation.
+// Tables of one tile are built by kb_small instead.
 __global__ void __launch_bounds__(kThreads) kb_stats_combine(const BatchTable *__restrict__ bt,
                                                              const Partial *__restrict__ part, uint32_t f32,
                                                              DevHeader *hdr, uint32_t *epoch)
@@ -62,7 +66,66 @@ __global__ void __launch_bounds__(kThreads) kb_stats_combine(const BatchTable *_
         *epoch = e;
     }
     const BatchTable &T = bt[blockIdx.x];
+    if (T.ntiles <= 1) return;
     stats_combine_body(part + T.part0, T.nparts, T.n, f32, hdr + blockIdx.x);
+}
+
+// A table of at most one tile, whole, in one block: validity, exact total
+// and lowest set bit (as k_stats + k_stats_combine), the header, then Alg. 2
+// on its n items with capacity Q and item weights n * q (group_build: the
+// table is a single group), and the light count.  The buckets and header
+// equal those of the tile pipeline.
+template <int F32>
+__global__ void __launch_bounds__(kThreads, 3) kb_small(const uint32_t *__restrict__ w, int vec,
+                                                        const BatchTable *__restrict__ bt,
+                                                        const BlockMap *__restrict__ map, DevHeader *hdr_all,
+                                                        uint4 *__restrict__ buckets)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    GroupSmem &S = *reinterpret_cast<GroupSmem *>(smem_raw);
+    __shared__ uint32_t s_status;
+    const BlockMap m = map[blockIdx.x];
+    const BatchTable &T = bt[m.table];
+    DevHeader *hdr = hdr_all + m.table;
+    const uint64_t N = T.n;
+    const uint32_t *wt = w + T.off;
+    const uint64_t first = (uint64_t)threadIdx.x * kItems;
+    uint32_t x[kItems];
+    load_items(wt, N, vec, first, x);
+    Acc a;
+    a.base = F32 ? INT_MAX : 0;
+    a.acc = 0;
+    a.flags = 0;
+    uint64_t a64 = 0;
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+        if (first + k < N) {
+            acc_take<F32>(a, a64, x[k]);
+            if (F32) acc_fold(a, a64);
+        }
+    }
+    acc_fold(a, a64);
+    a = acc_block_reduce(a);
+    if (threadIdx.x == 0) s_status = write_header(a, N, F32, hdr);
+    __syncthreads();
+    if (s_status) return;
+    const u128 Q = mk128(hdr->q_lo, hdr->q_hi);
+    const int beta = hdr->beta;
+    const uint32_t shift = hdr->shift;
+    u128 q[kItems];
+    uint32_t cl = 0;
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+        q[k] = first + k < N ? q_of(x[k], F32, beta) : (u128)0;
+        if (first + k < N && q[k] * (u128)N <= Q) ++cl;
+    }
+    uint32_t nl;
+    block_exclusive_scan_u32(cl, nl, S.cnt);
+    if (threadIdx.x == 0) hdr->n_light = nl;
+    const bool bad = bitlen128(Q) <= 52
+                         ? group_build<uint64_t>(S, q, Q, (uint32_t)N, N, first, 0, shift, buckets + T.off)
+                         : group_build<u128>(S, q, Q, (uint32_t)N, N, first, 0, shift, buckets + T.off);
+    if (bad) set_status(hdr, kEInternal);
 }
 
 template <int F32>
@@ -194,7 +257,7 @@ struct wrs_batch {
     Split *split;
     uint16_t *slist;
     uint4 *buckets;
-    BlockMap *map[7];      // stats, combine (unused), classify, tilescan, split, sweep, sample
+    BlockMap *map[7];      // stats, small tables, classify, tilescan, split, sweep, sample
     uint32_t nb[7];        // blocks of each launch
     uint32_t map_cap[7];
     int built;             // a build was enqueued
@@ -202,7 +265,7 @@ struct wrs_batch {
 
 namespace {
 
-enum { kMapStats = 0, kMapClassify = 2, kMapScan = 3, kMapSplit = 4, kMapSweep = 5, kMapSample = 6 };
+enum { kMapStats = 0, kMapSmall = 1, kMapClassify = 2, kMapScan = 3, kMapSplit = 4, kMapSweep = 5, kMapSample = 6 };
 
 // Offsets of the tables' weights: 4-weight (16-byte) aligned, in order.
 void batch_offsets(uint32_t ntables, const uint64_t *n, uint64_t *off)
@@ -240,6 +303,7 @@ wrs_status apply_groups(wrs_batch *b)
     for (uint32_t t = 0; t < b->ntables; ++t) {
         BatchTable &T = b->h[t];
         T.group = b->groups[batch_class(T.ntiles)];
+        if (T.ntiles <= 1) continue; // built whole by kb_small
         const uint32_t nblk = (T.ntiles + T.group - 1) / T.group;
         for (uint32_t i = 0; i < nblk; ++i) m.push_back(BlockMap{t, i});
     }
@@ -252,6 +316,16 @@ wrs_status batch_enqueue_build(wrs_batch *b, const uint32_t *w, uint32_t f32, cu
                                cudaEvent_t sweep1)
 {
     const int vec = (reinterpret_cast<uintptr_t>(w) % 16) == 0;
+    if (b->nb[kMapSmall]) {
+        const size_t gs = sizeof(GroupSmem);
+        if (f32) kb_small<1><<<b->nb[kMapSmall], kThreads, gs, s>>>(w, vec, b->d_tables, b->map[kMapSmall], b->hdr, b->buckets);
+        else kb_small<0><<<b->nb[kMapSmall], kThreads, gs, s>>>(w, vec, b->d_tables, b->map[kMapSmall], b->hdr, b->buckets);
+    }
+    if (b->nb[kMapStats] == 0) { // every table is small: the pipeline has no work
+        if (sweep0) cudaEventRecord(sweep0, s);
+        if (sweep1) cudaEventRecord(sweep1, s);
+        return launch_err();
+    }
     if (f32) kb_stats<1><<<b->nb[kMapStats], kThreads, 0, s>>>(w, vec, b->d_tables, b->map[kMapStats], b->part);
     else kb_stats<0><<<b->nb[kMapStats], kThreads, 0, s>>>(w, vec, b->d_tables, b->map[kMapStats], b->part);
     kb_stats_combine<<<b->ntables, kThreads, 0, s>>>(b->d_tables, b->part, f32, b->hdr, b->epoch);
@@ -270,6 +344,7 @@ wrs_status batch_enqueue_build(wrs_batch *b, const uint32_t *w, uint32_t f32, cu
 
 wrs_status batch_enqueue_sweep(wrs_batch *b, const uint32_t *w, uint32_t f32, cudaStream_t s)
 {
+    if (b->nb[kMapSweep] == 0) return WRS_OK;
     const int vec = (reinterpret_cast<uintptr_t>(w) % 16) == 0;
     const size_t smem = sizeof(SweepSmem);
     if (f32) kb_sweep<1><<<b->nb[kMapSweep], kThreads, smem, s>>>(w, vec, b->d_tables, b->map[kMapSweep], b->hdr, b->incl, b->split, b->slist, b->buckets);
@@ -285,9 +360,11 @@ wrs_status batch_kernel_attributes()
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) return WRS_EDEVICE;
     if (g_batch_attr_done[dev]) return WRS_OK;
-    const int bytes = (int)sizeof(SweepSmem);
+    const int bytes = (int)sizeof(SweepSmem), gbytes = (int)sizeof(GroupSmem);
     cudaError_t e = cudaFuncSetAttribute(kb_sweep<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sweep<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_small<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, gbytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_small<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, gbytes);
     if (e != cudaSuccess) return WRS_EDEVICE;
     g_batch_attr_done[dev] = true;
     return WRS_OK;
@@ -383,15 +460,17 @@ wrs_status wrs_batch_create(uint32_t ntables, const uint64_t *h_n, wrs_batch **o
     e = cudaMemset(b->ws, 0, o);
     if (e != cudaSuccess) { wrs_batch_free(b); return cuda_err(e); }
 
-    std::vector<BlockMap> ms, mc, mscan, msplit;
+    std::vector<BlockMap> ms, msmall, mc, mscan, msplit;
     for (uint32_t t = 0; t < ntables; ++t) {
         const BatchTable &T = b->h[t];
+        if (T.ntiles <= 1) { msmall.push_back(BlockMap{t, 0}); continue; } // one block builds it whole
         for (uint32_t i = 0; i < T.nparts; ++i) ms.push_back(BlockMap{t, i});
         for (uint32_t i = 0; i < (T.ntiles + kWarps - 1) / kWarps; ++i) mc.push_back(BlockMap{t, i});
         for (uint32_t i = 0; i < (T.ntiles + kScanChunk - 1) / kScanChunk; ++i) mscan.push_back(BlockMap{t, i});
         for (uint32_t i = 0; i < (T.ntiles + kThreads - 1) / kThreads; ++i) msplit.push_back(BlockMap{t, i});
     }
     st = upload_map(b, kMapStats, ms);
+    if (st == WRS_OK) st = upload_map(b, kMapSmall, msmall);
     if (st == WRS_OK) st = upload_map(b, kMapClassify, mc);
     if (st == WRS_OK) st = upload_map(b, kMapScan, mscan);
     if (st == WRS_OK) st = upload_map(b, kMapSplit, msplit);
@@ -527,7 +606,8 @@ wrs_status wrs_batch_tune(wrs_batch *b, const void *d_weights, wrs_dtype dtype, 
     const uint32_t f32 = dtype == WRS_F32;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     bool present[kBatchClasses] = {};
-    for (const BatchTable &T : b->h) present[batch_class(T.ntiles)] = true;
+    for (const BatchTable &T : b->h)
+        if (T.ntiles > 1) present[batch_class(T.ntiles)] = true; // one-tile tables: kb_small, no sweep
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         if (e0) cudaEventDestroy(e0);

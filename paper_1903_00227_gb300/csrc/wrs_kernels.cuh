@@ -319,6 +319,8 @@ __device__ bool f32_light(uint32_t v, uint64_t n, u128 Q, int beta)
     return nm <= (Q << dd);
 }
 
+__device__ __forceinline__ uint32_t write_header(const Acc &a, uint64_t n, uint32_t f32, DevHeader *hdr);
+
 __device__ __forceinline__ void stats_combine_body(const Partial *__restrict__ part, uint32_t nparts, uint64_t n,
                                                    uint32_t f32, DevHeader *hdr)
 {
@@ -332,7 +334,13 @@ __device__ __forceinline__ void stats_combine_body(const Partial *__restrict__ p
         acc_merge(a, b);
     }
     a = acc_block_reduce(a);
-    if (threadIdx.x != 0) return;
+    if (threadIdx.x == 0) write_header(a, n, f32, hdr);
+}
+
+// The table header from the exact total (thread 0): status, beta, Q, shift,
+// qp and the light threshold on the raw words.
+__device__ __forceinline__ uint32_t write_header(const Acc &a, uint64_t n, uint32_t f32, DevHeader *hdr)
+{
     uint32_t status = kOk;
     if (a.flags & kPartInvalid) status = kEInval;
     else if (a.flags & kPartOverflow) status = kEOverflow;
@@ -366,6 +374,7 @@ __device__ __forceinline__ void stats_combine_body(const Partial *__restrict__ p
     hdr->n_light = 0;
     __threadfence();
     hdr->status = status;
+    return status;
 }
 
 __global__ void __launch_bounds__(kThreads) k_stats_combine(const Partial *__restrict__ part, uint32_t nparts,
@@ -464,18 +473,43 @@ __device__ __forceinline__ void classify_body(const uint32_t *__restrict__ w, ui
             const uint64_t first = tile0 + c * kChunk + lane * kItems;
             uint32_t lm = 0, hm = 0;
             bool narrow = true;
+            uint32_t emin = 0xFFFFFFFFu, emax = 0;
 #pragma unroll
             for (int k = 0; k < kItems; ++k) {
                 if (first + k < n) {
                     if (x[k] <= light_max) lm |= 1u << k; else hm |= 1u << k;
                     if (F32) {
                         const uint32_t ex = (x[k] >> 23) & 0xFFu;
+                        emin = min(emin, ex);
+                        emax = max(emax, ex);
                         if ((ex ? (int)ex : 1) - 150 - beta > 37) narrow = false;
                     }
                 }
             }
             u128 L = 0, H = 0;
-            if (__all_sync(0xFFFFFFFFu, narrow)) { // every q below 2^61: eight of them fit 64 bits
+            uint32_t e0 = 0;
+            bool chunk_fast = false;
+            if (F32 && tile0 + (c + 1) * kChunk <= n) { // a full chunk (the same in every lane)
+                e0 = __reduce_min_sync(0xFFFFFFFFu, emin);
+                chunk_fast = e0 >= 1 && __reduce_max_sync(0xFFFFFFFFu, emax) - e0 <= 31;
+            }
+            if (chunk_fast) {
+                // every weight normal, exponents within 31 binades: m * 2^(e - e0)
+                // in 64 bits (one multiply-add each, below 2^58 per lane), then
+                // the warp's sums scaled to units of 2^beta (exact: every term
+                // is a multiple of 2^beta)
+                uint64_t l64 = 0, h64 = 0;
+#pragma unroll
+                for (int k = 0; k < kItems; ++k) {
+                    const uint64_t v = (uint64_t)((x[k] & 0x7FFFFFu) | 0x800000u) * (1u << ((x[k] >> 23) - e0));
+                    if ((lm >> k) & 1u) l64 += v; else h64 += v;
+                }
+                const int sh = (int)e0 - 150 - beta;
+                L = warp_sum128(l64);
+                H = warp_sum128(h64);
+                L = sh >= 0 ? L << sh : L >> (-sh);
+                H = sh >= 0 ? H << sh : H >> (-sh);
+            } else if (__all_sync(0xFFFFFFFFu, narrow)) { // every q below 2^61: eight of them fit 64 bits
                 uint64_t l64 = 0, h64 = 0;
 #pragma unroll
                 for (int k = 0; k < kItems; ++k) {
@@ -483,7 +517,8 @@ __device__ __forceinline__ void classify_body(const uint32_t *__restrict__ w, ui
                     if ((lm >> k) & 1u) l64 += q;
                     if ((hm >> k) & 1u) h64 += q;
                 }
-                L = l64; H = h64;
+                L = warp_sum128(l64);
+                H = warp_sum128(h64);
             } else {
 #pragma unroll
                 for (int k = 0; k < kItems; ++k) {
@@ -492,6 +527,8 @@ __device__ __forceinline__ void classify_body(const uint32_t *__restrict__ w, ui
                         if ((lm >> k) & 1u) L += q; else H += q;
                     }
                 }
+                L = warp_sum128(L);
+                H = warp_sum128(H);
             }
             // prefetch the next chunk (or the next tile's first) while reducing
             const uint64_t nf = c + 1 < (uint32_t)kChunks ? first + kChunk
@@ -516,8 +553,6 @@ __device__ __forceinline__ void classify_body(const uint32_t *__restrict__ w, ui
                 }
             }
             if (more) load_items(w, n, vec, nf, x);
-            L = warp_sum128(L);
-            H = warp_sum128(H);
             Lp += L; Hp += H;
             clp += cl; chp += ch;
         }

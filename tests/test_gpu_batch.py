@@ -195,3 +195,49 @@ def test_batch_argument_errors():
     with wrs.AliasBatch([10, 20]) as b:
         assert wrs.batch_sample(b.handle, 1, 0, 0, 0) == wrs.EINVAL  # never built
         assert wrs.batch_set_groups(b.handle, [0, 1, 1, 1, 1]) == wrs.EINVAL
+
+
+@pytest.mark.parametrize("dtype", ["f32", "u32"])
+def test_batch_of_only_one_tile_tables(dtype):
+    """Every table at most one tile: the one-block whole-table builder alone
+    (no tile pipeline launches); headers, light counts, buckets and samples
+    equal the oracle's and the single-table path's."""
+    sizes = [1, 2, 3, 7, 31, 32, 33, 255, 256, 257, 1000, 2047, 2048, 64, 1500]
+    ws = _weights(sizes, dtype, 90)
+    if dtype == "f32":  # degenerate shapes: all equal, one giant, subnormals, zeros
+        ws[5] = np.full(32, 0.25, np.float32)
+        ws[6] = np.concatenate([np.full(32, 1e-3, np.float32), np.array([1e6], np.float32)])
+        ws[13] = np.array([1e-45, 3e-45, 0.0, 2.0 ** -126] * 16, np.float32)
+    with wrs.AliasBatch(sizes) as b:
+        b.build(b.pack(_to_cuda(ws)))
+        rc, st = b.status()
+        assert rc == wrs.OK and st == [wrs.OK] * len(sizes)
+        _check_tables(b, ws)
+        for t, w in enumerate(ws):
+            qz, _ = O.build_table(w)
+            with wrs.AliasTable(len(w)) as single:
+                single.build(_to_cuda([w])[0])
+                want = single.info()
+            info = b.info(t)
+            assert (info.n_light, info.light_max, info.shift) == (want.n_light, want.light_max, want.shift), t
+        ks = [t * 313 + 3 for t in range(len(sizes))]
+        b.set_samples(ks)
+        out = b.sample(seed=5, stream_id=70)
+        torch.cuda.synchronize()
+        _check_samples(b, ws, ks, out, 5, 70)
+
+
+def test_one_tile_table_with_a_bad_weight_fails_alone():
+    sizes = [100, 2000, 5000]
+    ws = _weights(sizes, "f32", 11)
+    ws[0][17] = np.float32(np.nan)
+    with wrs.AliasBatch(sizes) as b:
+        b.build(b.pack(_to_cuda(ws)))
+        rc, st = b.status()
+        assert st[0] == wrs.EINVAL and st[1] == wrs.OK and st[2] == wrs.OK
+        thr, alias, _ = b.download()
+        for t in (1, 2):
+            _, tab = O.build_table(ws[t])
+            lo = b.offsets[t]
+            assert np.array_equal(thr[lo:lo + sizes[t]], tab.thr)
+            assert np.array_equal(alias[lo:lo + sizes[t]], tab.alias)
