@@ -1063,57 +1063,70 @@ __device__ __forceinline__ void sweep_body(const uint32_t *__restrict__ w, uint6
                 const uint32_t steps = min(per, M - d0);
                 u128 ej = j < b1 ? S.hkey[swz(j)] : (u128)0;
                 u128 di = i < nl ? S.okey[swz(i)] : D_end; // key of light i (D_end past the last)
-                for (uint32_t st = 0; st < steps; ++st) {
-                    const bool heavy_next = (j < b1) && (i >= a1 || ej <= di);
-                    if (narrow) {
-                        // Q < 2^64 (shift 0): a bucket's mass, a light's deficit
-                        // and a heavy's gap D - E (< Q when the build is sound,
-                        // checked in full) are 64-bit; only the keys are wider
-                        const uint64_t Q64 = lo64(Q);
+                // positions of heavies j and j + 1 (the first heavy after the
+                // stream tile past its last), kept in registers along the walk
+                const uint32_t hnext = split[s].next_heavy;
+                auto hpos = [&](uint32_t jj) -> uint32_t {
+                    return jj < hc ? (uint32_t)(sbase + S.hoff[jj]) : hnext;
+                };
+                uint32_t hp = hpos(j), hp1 = hpos(j + 1);
+                if (narrow) {
+                    // Q < 2^64 (shift 0): a bucket's mass, a light's deficit
+                    // and a heavy's gap D - E (< Q when the build is sound,
+                    // checked in full) are 64-bit; only the keys are wider
+                    const uint64_t Q64 = lo64(Q);
+                    for (uint32_t st = 0; st < steps; ++st) {
+                        const bool heavy_next = (j < b1) && (i >= a1 || ej <= di);
+                        uint32_t me, alias;
+                        uint64_t bw;
                         if (heavy_next) {
                             const u128 gap = di - ej;
                             if (hi64(gap) != 0 || lo64(gap) >= Q64) bad = true;
-                            const uint64_t bw = Q64 - lo64(gap);
-                            const uint32_t me = (uint32_t)(sbase + S.hoff[j]);
-                            const uint32_t nx = (j + 1 < hc) ? (uint32_t)(sbase + S.hoff[j + 1]) : split[s].next_heavy;
-                            if (nx == kNone && bw != Q64) bad = true;
-                            const uint32_t alias = (nx == kNone || bw == Q64) ? me : nx;
-                            table[me] = make_uint4((uint32_t)bw, (uint32_t)(bw >> 32), alias, 0u);
+                            bw = Q64 - lo64(gap);
+                            me = hp;
+                            if (hp1 == kNone && bw != Q64) bad = true;
+                            alias = (hp1 == kNone || bw == Q64) ? me : hp1;
                             ++j;
                             if (j < b1) ej = S.hkey[swz(j)];
+                            hp = hp1;
+                            hp1 = hpos(j + 1);
                         } else {
                             const u128 dn = (i + 1 < nl) ? S.okey[swz(i + 1)] : D_end;
                             const uint64_t def = lo64(dn) - lo64(di); // < Q: exact modulo 2^64
-                            const uint64_t nq = Q64 - def;
-                            const uint32_t me = (uint32_t)(tile0 + S.ooff[i]);
-                            const uint32_t alias = (def == 0) ? me : (uint32_t)(sbase + S.hoff[j]);
-                            table[me] = make_uint4((uint32_t)nq, (uint32_t)(nq >> 32), alias, 0u);
+                            bw = Q64 - def;
+                            me = (uint32_t)(tile0 + S.ooff[i]);
+                            alias = (def == 0) ? me : hp;
                             ++i;
                             di = dn;
                         }
-                        continue;
+                        table[me] = make_uint4((uint32_t)bw, (uint32_t)(bw >> 32), alias, 0u);
                     }
-                    if (heavy_next) {
-                        const u128 gap = di - ej;
-                        if (gap >= Q) bad = true;
-                        const u128 bw = Q - gap;
-                        const uint32_t me = (uint32_t)(sbase + S.hoff[j]);
-                        const uint32_t nx = (j + 1 < hc) ? (uint32_t)(sbase + S.hoff[j + 1]) : split[s].next_heavy;
-                        if (nx == kNone && bw != Q) bad = true;
-                        const uint32_t alias = (nx == kNone || bw == Q) ? me : nx;
+                } else {
+                    for (uint32_t st = 0; st < steps; ++st) {
+                        const bool heavy_next = (j < b1) && (i >= a1 || ej <= di);
+                        uint32_t me, alias;
+                        u128 bw;
+                        if (heavy_next) {
+                            const u128 gap = di - ej;
+                            if (gap >= Q) bad = true;
+                            bw = Q - gap;
+                            me = hp;
+                            if (hp1 == kNone && bw != Q) bad = true;
+                            alias = (hp1 == kNone || bw == Q) ? me : hp1;
+                            ++j;
+                            if (j < b1) ej = S.hkey[swz(j)];
+                            hp = hp1;
+                            hp1 = hpos(j + 1);
+                        } else { // light i; j < hc: heavy j is its current heavy
+                            const u128 dn = (i + 1 < nl) ? S.okey[swz(i + 1)] : D_end;
+                            bw = Q - (dn - di);
+                            me = (uint32_t)(tile0 + S.ooff[i]);
+                            alias = (bw == Q) ? me : hp;
+                            ++i;
+                            di = dn;
+                        }
                         const uint64_t thr = lo64(bw >> shift);
                         table[me] = make_uint4((uint32_t)thr, (uint32_t)(thr >> 32), alias, 0u);
-                        ++j;
-                        if (j < b1) ej = S.hkey[swz(j)];
-                    } else { // light i; j < hc: heavy j is its current heavy
-                        const u128 dn = (i + 1 < nl) ? S.okey[swz(i + 1)] : D_end;
-                        const u128 nq = Q - (dn - di);
-                        const uint32_t me = (uint32_t)(tile0 + S.ooff[i]);
-                        const uint32_t alias = (nq == Q) ? me : (uint32_t)(sbase + S.hoff[j]);
-                        const uint64_t thr = lo64(nq >> shift);
-                        table[me] = make_uint4((uint32_t)thr, (uint32_t)(thr >> 32), alias, 0u);
-                        ++i;
-                        di = dn;
                     }
                 }
             }
