@@ -466,38 +466,47 @@ __device__ __forceinline__ void classify_body(const uint32_t *__restrict__ w, ui
     if (t_first < ntiles) load_items(w, n, vec, (uint64_t)t_first * kTile + lane * kItems, x);
     for (uint32_t t = t_first; t < ntiles; t += t_stride) {
         const uint64_t tile0 = (uint64_t)t * kTile;
-        u128 Lp = 0, Hp = 0; // sums over the chunks so far (the same in every lane)
-        uint32_t clp = 0, chp = 0, fh = kNone;
+        u128 Lp = 0, Hp = 0;             // this lane's light and heavy sums over the tile (units of 2^beta)
+        uint32_t cl = 0, ch = 0;          // this lane's light and heavy counts
+        uint32_t chp = 0, fh = kNone;     // heavies before the chunk (kept while at most kSparse), first heavy
 #pragma unroll 1
         for (uint32_t c = 0; c < (uint32_t)kChunks; ++c) {
             const uint64_t first = tile0 + c * kChunk + lane * kItems;
-            uint32_t lm = 0, hm = 0;
-            bool narrow = true;
+            const bool full = tile0 + (c + 1) * kChunk <= n; // the same in every lane
+            uint32_t lm = 0, vm = 0xFFu;
             uint32_t emin = 0xFFFFFFFFu, emax = 0;
+            if (full) {
 #pragma unroll
-            for (int k = 0; k < kItems; ++k) {
-                if (first + k < n) {
-                    if (x[k] <= light_max) lm |= 1u << k; else hm |= 1u << k;
+                for (int k = 0; k < kItems; ++k) {
+                    if (x[k] <= light_max) lm |= 1u << k;
                     if (F32) {
-                        const uint32_t ex = (x[k] >> 23) & 0xFFu;
+                        const uint32_t ex = x[k] >> 23; // a valid word has its sign bit clear
                         emin = min(emin, ex);
                         emax = max(emax, ex);
-                        if ((ex ? (int)ex : 1) - 150 - beta > 37) narrow = false;
+                    }
+                }
+            } else {
+                vm = 0;
+#pragma unroll
+                for (int k = 0; k < kItems; ++k) {
+                    if (first + k < n) {
+                        vm |= 1u << k;
+                        if (x[k] <= light_max) lm |= 1u << k;
                     }
                 }
             }
-            u128 L = 0, H = 0;
-            uint32_t e0 = 0;
+            const uint32_t hm = vm & ~lm;
             bool chunk_fast = false;
-            if (F32 && tile0 + (c + 1) * kChunk <= n) { // a full chunk (the same in every lane)
+            uint32_t e0 = 0;
+            if (F32 && full) {
                 e0 = __reduce_min_sync(0xFFFFFFFFu, emin);
                 chunk_fast = e0 >= 1 && __reduce_max_sync(0xFFFFFFFFu, emax) - e0 <= 31;
             }
             if (chunk_fast) {
                 // every weight normal, exponents within 31 binades: m * 2^(e - e0)
                 // in 64 bits (one multiply-add each, below 2^58 per lane), then
-                // the warp's sums scaled to units of 2^beta (exact: every term
-                // is a multiple of 2^beta)
+                // scaled to units of 2^beta (exact: every term q * 2^-sh is a
+                // multiple of 2^-sh when sh < 0)
                 uint64_t l64 = 0, h64 = 0;
 #pragma unroll
                 for (int k = 0; k < kItems; ++k) {
@@ -505,65 +514,74 @@ __device__ __forceinline__ void classify_body(const uint32_t *__restrict__ w, ui
                     if ((lm >> k) & 1u) l64 += v; else h64 += v;
                 }
                 const int sh = (int)e0 - 150 - beta;
-                L = warp_sum128(l64);
-                H = warp_sum128(h64);
-                L = sh >= 0 ? L << sh : L >> (-sh);
-                H = sh >= 0 ? H << sh : H >> (-sh);
-            } else if (__all_sync(0xFFFFFFFFu, narrow)) { // every q below 2^61: eight of them fit 64 bits
-                uint64_t l64 = 0, h64 = 0;
-#pragma unroll
-                for (int k = 0; k < kItems; ++k) {
-                    const uint64_t q = q64_of(x[k], F32, beta);
-                    if ((lm >> k) & 1u) l64 += q;
-                    if ((hm >> k) & 1u) h64 += q;
-                }
-                L = warp_sum128(l64);
-                H = warp_sum128(h64);
+                Lp += sh >= 0 ? (u128)l64 << sh : (u128)(l64 >> (-sh));
+                Hp += sh >= 0 ? (u128)h64 << sh : (u128)(h64 >> (-sh));
             } else {
+                bool narrow = true; // every q below 2^61: eight of them fit 64 bits
+                if (F32) {
 #pragma unroll
-                for (int k = 0; k < kItems; ++k) {
-                    if (((lm | hm) >> k) & 1u) {
-                        const u128 q = q_of(x[k], F32, beta);
-                        if ((lm >> k) & 1u) L += q; else H += q;
+                    for (int k = 0; k < kItems; ++k) {
+                        const uint32_t ex = (x[k] >> 23) & 0xFFu;
+                        if (((vm >> k) & 1u) && (ex ? (int)ex : 1) - 150 - beta > 37) narrow = false;
                     }
                 }
-                L = warp_sum128(L);
-                H = warp_sum128(H);
+                if (narrow) {
+                    uint64_t l64 = 0, h64 = 0;
+#pragma unroll
+                    for (int k = 0; k < kItems; ++k) {
+                        const uint64_t q = q64_of(x[k], F32, beta);
+                        if ((lm >> k) & 1u) l64 += q;
+                        if ((hm >> k) & 1u) h64 += q;
+                    }
+                    Lp += l64;
+                    Hp += h64;
+                } else {
+#pragma unroll
+                    for (int k = 0; k < kItems; ++k) {
+                        if ((vm >> k) & 1u) {
+                            const u128 q = q_of(x[k], F32, beta);
+                            if ((lm >> k) & 1u) Lp += q; else Hp += q;
+                        }
+                    }
+                }
             }
-            // prefetch the next chunk (or the next tile's first) while reducing
+            cl += (uint32_t)__popc(lm);
+            ch += (uint32_t)__popc(hm);
+            // prefetch the next chunk (or the next tile's first)
             const uint64_t nf = c + 1 < (uint32_t)kChunks ? first + kChunk
                                                           : (uint64_t)(t + t_stride) * kTile + lane * kItems;
             const bool more = c + 1 < (uint32_t)kChunks || t + t_stride < ntiles;
-            const uint32_t cl = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)__popc(lm));
-            const uint32_t ch = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)__popc(hm));
-            const uint32_t hb = __ballot_sync(0xFFFFFFFFu, hm != 0);
-            if (fh == kNone && hb) {
-                const int src = __ffs(hb) - 1;
-                const uint32_t hs = __shfl_sync(0xFFFFFFFFu, hm, src);
-                fh = c * kChunk + (uint32_t)src * kItems + (uint32_t)(__ffs(hs) - 1);
-            }
-            if (chp < (uint32_t)kSparse && hb) { // offsets of the first heavies, in order
-                uint32_t pos = chp + warp_excl_scan_u32((uint32_t)__popc(hm));
+            if (chp <= (uint32_t)kSparse || fh == kNone) {
+                const uint32_t hb = __ballot_sync(0xFFFFFFFFu, hm != 0);
+                if (fh == kNone && hb) {
+                    const int src = __ffs(hb) - 1;
+                    const uint32_t hs = __shfl_sync(0xFFFFFFFFu, hm, src);
+                    fh = c * kChunk + (uint32_t)src * kItems + (uint32_t)(__ffs(hs) - 1);
+                }
+                if (chp <= (uint32_t)kSparse && hb) { // offsets of the first heavies, in order
+                    uint32_t pos = chp + warp_excl_scan_u32((uint32_t)__popc(hm));
 #pragma unroll
-                for (int k = 0; k < kItems; ++k) {
-                    if ((hm >> k) & 1u) {
-                        if (pos < (uint32_t)kSparse) list[pos] = (uint16_t)(c * kChunk + lane * kItems + k);
-                        ++pos;
+                    for (int k = 0; k < kItems; ++k) {
+                        if ((hm >> k) & 1u) {
+                            if (pos < (uint32_t)kSparse) list[pos] = (uint16_t)(c * kChunk + lane * kItems + k);
+                            ++pos;
+                        }
                     }
+                    chp += __reduce_add_sync(0xFFFFFFFFu, (uint32_t)__popc(hm));
                 }
             }
             if (more) load_items(w, n, vec, nf, x);
-            Lp += L; Hp += H;
-            clp += cl; chp += ch;
         }
+        const u128 L = warp_sum128(Lp), H = warp_sum128(Hp);
+        const uint32_t tl = __reduce_add_sync(0xFFFFFFFFu, cl), th = __reduce_add_sync(0xFFFFFFFFu, ch);
         __syncwarp();
         if (lane == 0) {
             TileSum a;
-            a.l_lo = lo64(Lp); a.l_hi = hi64(Lp); a.h_lo = lo64(Hp); a.h_hi = hi64(Hp);
-            a.cl = clp; a.nheavy = chp; a.first_heavy = fh; a.pad = 0;
+            a.l_lo = lo64(L); a.l_hi = hi64(L); a.h_lo = lo64(H); a.h_hi = hi64(H);
+            a.cl = tl; a.nheavy = th; a.first_heavy = fh; a.pad = 0;
             tilesum_st(agg + t, a);
         }
-        if (chp <= (uint32_t)kSparse && lane < chp) slist[(uint64_t)t * kSparse + lane] = list[lane];
+        if (th <= (uint32_t)kSparse && lane < th) slist[(uint64_t)t * kSparse + lane] = list[lane];
         __syncwarp();
     }
 }
