@@ -168,9 +168,9 @@ __device__ Acc acc_block_reduce(Acc a)
     return a; // valid in thread 0
 }
 
-// Add the exact value S * 2^(e0 - 150) of a chunk, whose lowest set bit is
-// at 2^(e0 - 150 + ctz(o)), to an accumulator kept in units of 2^base (base:
-// the lowest set bit seen so far).
+// Add the exact value S * 2^(e0 - 150) of some weights, whose lowest set bit
+// is at 2^(e0 - 150 + ctz(o)), to an accumulator kept in units of 2^base
+// (base: the lowest set bit seen so far).
 __device__ __forceinline__ void acc_add_chunk(Acc &a, uint64_t S, uint64_t o, int e0)
 {
     const int lsb = e0 - 150 + __ffsll((long long)o) - 1;
@@ -189,12 +189,12 @@ __device__ __forceinline__ void acc_add_chunk(Acc &a, uint64_t S, uint64_t o, in
 
 // Block `bid` of `nblk` blocks sharing the weights of one table; thread 0
 // writes the block's partial to *out.  Binary32 weights go in warp chunks
-// of 256 (lane l: weights 8l .. 8l+7): when every weight of a chunk is a
-// normal number and their exponents span at most 31 binades, the chunk's
-// exact sum is formed in 64 bits as sum m * 2^(e - e0) (e0: the chunk's
-// smallest exponent; one multiply-add per weight, below 2^63 over the warp)
-// and its lowest set bit from the OR of those terms; any other chunk takes
-// the exact per-weight path.
+// of 256 (lane l: weights 8l .. 8l+7): when each of a lane's eight is a
+// normal number and the exponents of a lane's eight span at most 31
+// binades, the lane forms their exact sum in 64 bits as sum m * 2^(e - e0)
+// (e0: its smallest exponent; one multiply-add per weight) and their lowest
+// set bit from the OR of those terms, and adds it to its accumulator; other
+// weights take the exact per-weight path.
 template <int F32>
 __device__ __forceinline__ void stats_body(const uint32_t *__restrict__ w, uint64_t n, int vec, uint32_t bid,
                                            uint32_t nblk, Partial *__restrict__ out)
@@ -227,8 +227,6 @@ __device__ __forceinline__ void stats_body(const uint32_t *__restrict__ w, uint6
         const uint32_t lane = threadIdx.x & 31;
         const uint64_t nchunks = (n + kChunk - 1) / kChunk;
         const uint64_t cw = (uint64_t)nblk * kWarps;
-        Acc f; // the fast chunks' sum (the same in every lane)
-        f.base = INT_MAX; f.acc = 0; f.flags = 0;
         uint32_t vmax = 0; // any word >= 0x7F800000 is Inf, NaN or has the sign bit set
         uint64_t c = (uint64_t)bid * kWarps + (threadIdx.x >> 5);
         uint32_t x[kItems];
@@ -238,7 +236,7 @@ __device__ __forceinline__ void stats_body(const uint32_t *__restrict__ w, uint6
             uint32_t xn[kItems];
             const bool more = c + cw < nchunks;
             if (more) load_items(w, n, vec, (c + cw) * kChunk + lane * kItems, xn);
-            bool fast = (c + 1) * kChunk <= n; // a full chunk (the same in every lane)
+            bool fast = (c + 1) * kChunk <= n; // a full chunk
             uint32_t e0 = 0;
             if (fast) {
                 uint32_t emin = 0xFFFFFFFFu, emax = 0;
@@ -249,9 +247,8 @@ __device__ __forceinline__ void stats_body(const uint32_t *__restrict__ w, uint6
                     emin = min(emin, ex);
                     emax = max(emax, ex);
                 }
-                e0 = __reduce_min_sync(0xFFFFFFFFu, emin);
-                const uint32_t e1 = __reduce_max_sync(0xFFFFFFFFu, emax);
-                fast = e0 >= 1 && e1 < 255 && e1 - e0 <= 31; // all normal, finite, 31 binades
+                e0 = emin;
+                fast = e0 >= 1 && emax < 255 && emax - e0 <= 31; // this lane's eight: normal, finite, 31 binades
             }
             if (fast) {
                 uint64_t sum = 0, orr = 0;
@@ -262,14 +259,7 @@ __device__ __forceinline__ void stats_body(const uint32_t *__restrict__ w, uint6
                     sum += v;
                     orr |= v;
                 }
-                // warp sum (< 2^63) by 16-bit limbs, warp OR by halves
-                uint64_t S = 0;
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    S += (uint64_t)__reduce_add_sync(0xFFFFFFFFu, (uint32_t)(sum >> (16 * q)) & 0xFFFFu) << (16 * q);
-                const uint64_t O = (uint64_t)__reduce_or_sync(0xFFFFFFFFu, (uint32_t)orr) |
-                                   ((uint64_t)__reduce_or_sync(0xFFFFFFFFu, (uint32_t)(orr >> 32)) << 32);
-                acc_add_chunk(f, S, O, (int)e0);
+                acc_add_chunk(a, sum, orr, (int)e0); // this lane's eight terms (orr > 0: every m has its top bit)
             } else {
 #pragma unroll
                 for (int k = 0; k < kItems; ++k) {
@@ -285,7 +275,6 @@ __device__ __forceinline__ void stats_body(const uint32_t *__restrict__ w, uint6
             }
         }
         if (vmax >= 0x7F800000u) a.flags |= kPartInvalid;
-        if (lane == 0) acc_merge(a, f);
     }
     a = acc_block_reduce(a);
     if (threadIdx.x == 0) {
