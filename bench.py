@@ -817,7 +817,7 @@ def run_e2e(args, torch, wrs, table, weights, names, stream, ws):
 
     # serial: one table, one step at a time (first call allocates the staging buffers)
     sh0 = stream.cuda_stream
-    times, t_up, t_down, t_bld = [], [], [], []
+    times, t_up, t_down, t_bld, per_step = [], [], [], [], []
     for i in range(K + 1):
         name = names[i % len(names)]
         torch.cuda.synchronize()
@@ -833,6 +833,9 @@ def run_e2e(args, torch, wrs, table, weights, names, stream, ws):
             t_up.append(e0.elapsed_time(em))
             t_down.append(em.elapsed_time(e1))
             t_bld.append(sum(table.stage_ms().values()))  # the build's own kernels (stage events)
+            per_step.append({"input": name, "upload_build_ms": t_up[-1], "build_kernels_ms": t_bld[-1],
+                             "upload_gbs": 4 * n / max(1e-9, (t_up[-1] - t_bld[-1]) * 1e-3) / 1e9,
+                             "sample_download_ms": t_down[-1]})
     t_serial = reduce_max([statistics.mean(times)], "cuda")[0]
 
     # pipelined: two table objects on two streams
@@ -868,7 +871,7 @@ def run_e2e(args, torch, wrs, table, weights, names, stream, ws):
             "d2h_bytes_per_step": 4 * k, "ms_per_step": t_pipe, "steps": steps,
             "serial": {"value": ws * n / (t_serial * 1e-3) / 1e9, "ms_per_step": t_serial,
                        "upload_build_ms": statistics.mean(t_up), "build_kernels_ms": statistics.mean(t_bld),
-                       "sample_download_ms": statistics.mean(t_down)},
+                       "sample_download_ms": statistics.mean(t_down), "steps": per_step},
             "host_link_gbs": link,
             "note": "wrs_table_build_host (H2D of the weights) + wrs_sample_host (D2H of the samples) per step; "
                     "two table objects and two streams, step i+1's upload and build issued before step i's "
