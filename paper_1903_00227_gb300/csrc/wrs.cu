@@ -23,7 +23,7 @@ constexpr int kOpSlots = 8; // streams whose last operation on a table is tracke
 // whole device.
 struct OpLog {
     std::mutex mu;
-    cudaStream_t priv = nullptr;  // library-private stream: read-backs, uploads, frees
+    cudaStream_t priv = nullptr;  // library-private stream (read-backs, uploads, frees), made on first need
     cudaEvent_t build_ev = nullptr;
     bool built = false;
     cudaStream_t slot_stream[kOpSlots] = {};
@@ -165,12 +165,22 @@ wrs_status wait_build(const wrs_table *t)
     return L.built ? cuda_err(cudaEventSynchronize(L.build_ev)) : WRS_OK;
 }
 
+// The table's private stream, created on first need: a table that is only
+// built and sampled (a serving pool holds thousands) owns no stream.
+wrs_status ensure_priv(OpLog &L)
+{
+    if (L.priv) return WRS_OK;
+    return cuda_err(cudaStreamCreateWithFlags(&L.priv, cudaStreamNonBlocking));
+}
+
 // Make the private stream wait for every tracked operation on the table
 // (device-side ordering; the host does not wait).
 wrs_status order_after_all(const wrs_table *t)
 {
     OpLog &L = *t->log;
     std::lock_guard<std::mutex> lock(L.mu);
+    const wrs_status st = ensure_priv(L);
+    if (st != WRS_OK) return st;
     for (int k = 0; k < L.nslots; ++k) {
         cudaError_t e = cudaStreamWaitEvent(L.priv, L.slot_ev[k], 0);
         if (e != cudaSuccess) return cuda_err(e);
@@ -183,6 +193,11 @@ wrs_status order_after_all(const wrs_table *t)
 wrs_status read_back(const wrs_table *t, void *h, const void *d, size_t bytes)
 {
     wrs_status st = wait_build(t);
+    if (st != WRS_OK) return st;
+    {
+        std::lock_guard<std::mutex> lock(t->log->mu);
+        st = ensure_priv(*t->log);
+    }
     if (st != WRS_OK) return st;
     cudaError_t e = cudaMemcpyAsync(h, d, bytes, cudaMemcpyDeviceToHost, t->log->priv);
     if (e == cudaSuccess) e = cudaStreamSynchronize(t->log->priv);
@@ -327,6 +342,10 @@ wrs_status wrs_table_create(uint64_t capacity_n, wrs_table **out)
         delete t;
         return cuda_err(e);
     }
+    // the memory is ready for every stream; the private stream is made again
+    // on first need
+    cudaStreamDestroy(ps);
+    t->log->priv = nullptr;
     *out = t;
     return WRS_OK;
 }
