@@ -104,6 +104,33 @@ wrs_status wrs_table_create(uint64_t capacity_n, wrs_table **out);
 wrs_status wrs_table_build(wrs_table *t, const void *d_weights, uint64_t n,
                            wrs_dtype dtype, void *stream);
 
+/* Build options.  The table does not depend on any of them (Alg. 3 gives
+ * Alg. 2's table for every split count, Sec. 4.2); they choose how the work
+ * is cut and which exact arithmetic the pack uses.
+ *   splits  number of subproblems of Alg. 3's pack (one per block of the
+ *           sweep, each a run of consecutive 2048-weight tiles); 0: the
+ *           library's choice (8 tiles per subproblem); at most the number
+ *           of tiles, ceil(n / 2048)
+ *   tile    0 or 2048 (the tile is fixed)
+ *   acc     WRS_ACC_AUTO: 64-bit bucket arithmetic when Q < 2^64, else
+ *           128-bit; WRS_ACC_U64: the build fails with WRS_EOVERFLOW (in
+ *           the status word) when Q >= 2^64; WRS_ACC_U128: 128-bit
+ *           arithmetic throughout.  Keys are 128-bit in every mode.  There
+ *           is no binary64 mode: every mode is exact.
+ *   flags   0 */
+typedef enum { WRS_ACC_AUTO = 0, WRS_ACC_U64 = 1, WRS_ACC_U128 = 2 } wrs_acc;
+typedef struct {
+    uint32_t splits;
+    uint32_t tile;
+    uint32_t acc;   /* a wrs_acc */
+    uint32_t flags;
+} wrs_build_opts;
+
+/* wrs_table_build with options (NULL: the defaults).  Errors returned at
+ * once: WRS_EINVAL (as wrs_table_build, or an option out of range). */
+wrs_status wrs_table_build_opts(wrs_table *t, const void *d_weights, uint64_t n, wrs_dtype dtype,
+                                const wrs_build_opts *opts, void *stream);
+
 /* Build the alias table of n weights with PSA+ (Sec. 4.2 "Performance
  * Optimization in Practice"): every tile of 2048 consecutive items first runs
  * Alg. 2 on its own items, in the global units (capacity Q, item i weighs

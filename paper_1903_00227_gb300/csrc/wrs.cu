@@ -204,7 +204,15 @@ wrs_status read_back(const wrs_table *t, void *h, const void *d, size_t bytes)
     return cuda_err(e);
 }
 
-wrs_status enqueue_build(wrs_table *t, const void *d_weights, uint64_t n, wrs_dtype dtype, cudaStream_t s)
+// Build options after validation: own tiles per sweep block (one subproblem
+// of Alg. 3 each), the accumulator mode.
+struct BuildOpts {
+    uint32_t group = kSweepTiles;
+    int acc = WRS_ACC_AUTO;
+};
+
+wrs_status enqueue_build(wrs_table *t, const void *d_weights, uint64_t n, wrs_dtype dtype, cudaStream_t s,
+                         const BuildOpts &o = BuildOpts())
 {
     {
         const wrs_status st = set_kernel_attributes();
@@ -243,11 +251,13 @@ wrs_status enqueue_build(wrs_table *t, const void *d_weights, uint64_t n, wrs_dt
                                             wait_limit, skip_tile);
     if (tm) cudaEventRecord(t->ev[4], s);
     k_split<<<(ntiles + kThreads - 1) / kThreads, kThreads, 0, s>>>(t->incl, ntiles, n, t->hdr, t->split);
+    if (o.acc == WRS_ACC_U64) k_require_u64<<<1, 32, 0, s>>>(t->hdr);
     if (tm) cudaEventRecord(t->ev[5], s);
     const size_t sweep_smem = sizeof(SweepSmem);
-    const uint32_t sweep_blocks = (ntiles + kSweepTiles - 1) / kSweepTiles;
-    if (f32) k_sweep<1><<<sweep_blocks, kThreads, sweep_smem, s>>>(w, n, vec, t->hdr, t->incl, t->split, t->slist, ntiles, t->buckets);
-    else k_sweep<0><<<sweep_blocks, kThreads, sweep_smem, s>>>(w, n, vec, t->hdr, t->incl, t->split, t->slist, ntiles, t->buckets);
+    const uint32_t sweep_blocks = (ntiles + o.group - 1) / o.group;
+    const int wide = o.acc == WRS_ACC_U128;
+    if (f32) k_sweep<1><<<sweep_blocks, kThreads, sweep_smem, s>>>(w, n, vec, t->hdr, t->incl, t->split, t->slist, ntiles, t->buckets, o.group, wide);
+    else k_sweep<0><<<sweep_blocks, kThreads, sweep_smem, s>>>(w, n, vec, t->hdr, t->incl, t->split, t->slist, ntiles, t->buckets, o.group, wide);
     if (tm) cudaEventRecord(t->ev[6], s);
     t->timed_build = tm;
     wrs_status st = launch_err();
@@ -356,6 +366,25 @@ wrs_status wrs_table_build(wrs_table *t, const void *d_weights, uint64_t n, wrs_
     if (dtype != WRS_U32 && dtype != WRS_F32) return WRS_EINVAL;
     if ((reinterpret_cast<uintptr_t>(d_weights) % 4) != 0) return WRS_EINVAL;
     return enqueue_build(t, d_weights, n, dtype, static_cast<cudaStream_t>(stream));
+}
+
+wrs_status wrs_table_build_opts(wrs_table *t, const void *d_weights, uint64_t n, wrs_dtype dtype,
+                                const wrs_build_opts *opts, void *stream)
+{
+    if (!t || !d_weights || n == 0 || n > t->cap) return WRS_EINVAL;
+    if (dtype != WRS_U32 && dtype != WRS_F32) return WRS_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_weights) % 4) != 0) return WRS_EINVAL;
+    BuildOpts o;
+    if (opts) {
+        if (opts->flags != 0) return WRS_EINVAL;
+        if (opts->tile != 0 && opts->tile != (uint32_t)kTile) return WRS_EINVAL;
+        if (opts->acc != WRS_ACC_AUTO && opts->acc != WRS_ACC_U64 && opts->acc != WRS_ACC_U128) return WRS_EINVAL;
+        const uint32_t ntiles = (uint32_t)((n + kTile - 1) / kTile);
+        if (opts->splits > ntiles) return WRS_EINVAL;
+        if (opts->splits) o.group = (ntiles + opts->splits - 1) / opts->splits;
+        o.acc = opts->acc;
+    }
+    return enqueue_build(t, d_weights, n, dtype, static_cast<cudaStream_t>(stream), o);
 }
 
 wrs_status wrs_build(const void *d_weights, uint64_t n, wrs_dtype dtype, void *stream, wrs_table **out)
@@ -727,8 +756,8 @@ extern "C" wrs_status wrs_build_noalloc(const void *d_weights, uint64_t n, wrs_d
                                             g_wait_limit.load(), kNone);
     k_split<<<(ntiles + kThreads - 1) / kThreads, kThreads, 0, s>>>(incl, ntiles, n, hdr, split);
     const uint32_t sweep_blocks = (ntiles + kSweepTiles - 1) / kSweepTiles;
-    if (f32) k_sweep<1><<<sweep_blocks, kThreads, sizeof(SweepSmem), s>>>(w, n, vec, hdr, incl, split, slist, ntiles, buckets);
-    else k_sweep<0><<<sweep_blocks, kThreads, sizeof(SweepSmem), s>>>(w, n, vec, hdr, incl, split, slist, ntiles, buckets);
+    if (f32) k_sweep<1><<<sweep_blocks, kThreads, sizeof(SweepSmem), s>>>(w, n, vec, hdr, incl, split, slist, ntiles, buckets, kSweepTiles, 0);
+    else k_sweep<0><<<sweep_blocks, kThreads, sizeof(SweepSmem), s>>>(w, n, vec, hdr, incl, split, slist, ntiles, buckets, kSweepTiles, 0);
     return launch_err();
 }
 

@@ -953,7 +953,8 @@ template <int F32>
 __device__ __forceinline__ void sweep_body(const uint32_t *__restrict__ w, uint64_t n, int vec, DevHeader *hdr,
                                            const TileSum *__restrict__ incl, const Split *__restrict__ split,
                                            const uint16_t *__restrict__ slist, uint32_t ntiles,
-                                           uint4 *__restrict__ table, uint32_t c_first, uint32_t c_last)
+                                           uint4 *__restrict__ table, uint32_t c_first, uint32_t c_last,
+                                           bool force_wide = false)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SweepSmem &S = *reinterpret_cast<SweepSmem *>(smem_raw);
@@ -963,7 +964,7 @@ __device__ __forceinline__ void sweep_body(const uint32_t *__restrict__ w, uint6
     const uint32_t light_max = hdr->light_max;
     const int beta = hdr->beta;
     const uint32_t shift = hdr->shift;
-    const bool narrow = shift == 0; // Q < 2^64, the same for the whole grid
+    const bool narrow = shift == 0 && !force_wide; // Q < 2^64, the same for the whole grid
     bool bad = false;
 
     uint32_t x[kItems], y[kItems];
@@ -1145,15 +1146,26 @@ __device__ __forceinline__ void sweep_body(const uint32_t *__restrict__ w, uint6
     if (bad) set_status(hdr, kEInternal);
 }
 
+// Block b packs own tiles [b * group, (b + 1) * group): one subproblem of
+// Alg. 3 per block (group = kSweepTiles unless the caller asks for a split
+// count); force_wide runs the 128-bit walk even when Q < 2^64.
 template <int F32>
 __global__ void __launch_bounds__(kThreads, 3) k_sweep(const uint32_t *__restrict__ w, uint64_t n, int vec,
                                                        DevHeader *hdr, const TileSum *__restrict__ incl,
                                                        const Split *__restrict__ split,
                                                        const uint16_t *__restrict__ slist, uint32_t ntiles,
-                                                       uint4 *__restrict__ table)
+                                                       uint4 *__restrict__ table, uint32_t group, int force_wide)
 {
-    const uint32_t c_first = blockIdx.x * kSweepTiles;
-    sweep_body<F32>(w, n, vec, hdr, incl, split, slist, ntiles, table, c_first, min(c_first + kSweepTiles, ntiles));
+    const uint32_t c_first = blockIdx.x * group;
+    sweep_body<F32>(w, n, vec, hdr, incl, split, slist, ntiles, table, c_first, min(c_first + group, ntiles),
+                    force_wide != 0);
+}
+
+// The exact sum was asked to fit 64 bits (accumulator mode U64): Q >= 2^64
+// fails the build with WRS_EOVERFLOW before the sweep.
+__global__ void k_require_u64(DevHeader *hdr)
+{
+    if (threadIdx.x == 0 && hdr->status == 0 && hdr->q_hi != 0) set_status(hdr, kEOverflow);
 }
 
 // ----------------------------------------------------------- k_sample

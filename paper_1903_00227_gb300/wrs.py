@@ -57,6 +57,7 @@ _PTBL = ctypes.POINTER(ctypes.c_void_p)
 _sig = {
     "wrs_table_create": ([_U64, _PTBL], _I),
     "wrs_table_build": ([_TBL, _P, _U64, _I, _P], _I),
+    "wrs_table_build_opts": ([_TBL, _P, _U64, _I, _P, _P], _I),
     "wrs_table_build_psa_plus": ([_TBL, _P, _U64, _I, _P], _I),
     "wrs_table_psa_plus_leftovers": ([_TBL, ctypes.POINTER(ctypes.c_uint64)], _I),
     "wrs_build": ([_P, _U64, _I, _P, _PTBL], _I),
@@ -133,6 +134,21 @@ def table_create(capacity_n: int):
 
 def table_build(t, d_weights: int, n: int, dtype: int, stream: int = 0) -> int:
     return _lib.wrs_table_build(t, d_weights, n, dtype, stream)
+
+
+ACC_AUTO, ACC_U64, ACC_U128 = range(3)
+
+
+class BuildOpts(ctypes.Structure):
+    """wrs_build_opts: split count (0: the library's choice), tile (0 or
+    2048), accumulator mode, flags (0)."""
+    _fields_ = [("splits", ctypes.c_uint32), ("tile", ctypes.c_uint32), ("acc", ctypes.c_uint32),
+                ("flags", ctypes.c_uint32)]
+
+
+def table_build_opts(t, d_weights: int, n: int, dtype: int, opts: "BuildOpts | None", stream: int = 0) -> int:
+    return _lib.wrs_table_build_opts(t, d_weights, n, dtype, ctypes.byref(opts) if opts is not None else None,
+                                     stream)
 
 
 def table_build_psa_plus(t, d_weights: int, n: int, dtype: int, stream: int = 0) -> int:
@@ -361,6 +377,17 @@ class AliasTable:
         n = weights.numel()
         _check(table_build(self.handle, weights.data_ptr(), n, _dtype_code(weights), _stream_handle(stream)),
                "wrs_table_build")
+        self.n = n
+        return self
+
+    def build_opts(self, weights, splits: int = 0, acc: int = 0, tile: int = 0, stream=None) -> "AliasTable":
+        """wrs_table_build_opts: the same table for every split count and
+        accumulator mode; they choose how the work is cut."""
+        _require_cuda(weights, "weights")
+        n = weights.numel()
+        o = BuildOpts(splits, tile, acc, 0)
+        _check(table_build_opts(self.handle, weights.data_ptr(), n, _dtype_code(weights), o, _stream_handle(stream)),
+               "wrs_table_build_opts")
         self.n = n
         return self
 

@@ -267,3 +267,32 @@ def test_host_entry_points_double_buffered():
     finally:
         for t in tables:
             t.free()
+
+
+def test_build_options_do_not_change_the_table():
+    """Alg. 3's table is Alg. 2's for every split count (reading 2): the
+    first configuration's 64 splits, one split, a few, one per tile, and the
+    128-bit walk forced, all give the oracle's table; accumulator mode U64
+    fails only when Q >= 2^64."""
+    cases = [WL.u32_uniform(1_000_000, 1), WL.f32_zipf(300_001, 1.5, 8), WL.f32_uniform(70_000, 9)]
+    for w in cases:
+        qz, tab = O.build_table(w)
+        ntiles = -(-len(w) // 2048)
+        w_dev = G.to_device(w)
+        with wrs.AliasTable(len(w)) as t:
+            for splits in sorted({0, 1, 2, 3, 64, ntiles} & set(range(ntiles + 1))):
+                for acc in (wrs.ACC_AUTO, wrs.ACC_U128):
+                    t.build_opts(w_dev, splits=splits, acc=acc)
+                    assert t.status() == wrs.OK, (splits, acc)
+                    thr, alias, _ = t.download()
+                    assert np.array_equal(thr, tab.thr) and np.array_equal(alias, tab.alias), (len(w), splits, acc)
+            t.build_opts(w_dev, acc=wrs.ACC_U64)
+            assert t.status() == (wrs.OK if qz.Q < 1 << 64 else wrs.EOVERFLOW)
+            got = G.gpu_samples(t.build(w_dev), 5000, seed=3) if qz.Q >= 1 << 64 else None
+        if got is not None:  # a failed build does not stick: the next plain build is whole
+            assert np.array_equal(got, O.sample(tab.thr, tab.alias, tab.Qp, 5000, 3, 0))
+    with wrs.AliasTable(10) as t:
+        w_dev = G.to_device(np.ones(10, np.uint32))
+        for bad in (wrs.BuildOpts(2, 0, 0, 0), wrs.BuildOpts(0, 1024, 0, 0), wrs.BuildOpts(0, 0, 3, 0),
+                    wrs.BuildOpts(0, 0, 0, 1)):
+            assert wrs.table_build_opts(t.handle, w_dev.data_ptr(), 10, wrs.U32, bad, 0) == wrs.EINVAL
