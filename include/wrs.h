@@ -227,6 +227,31 @@ void wrs_table_free(wrs_table *t);
 /* Static string for a status code. */
 const char *wrs_status_str(wrs_status s);
 
+/* Check build.  libwrs_check.so is this library compiled with WRS_CHECK=1,
+ * with the same entry points and the same tables, for verification (it is
+ * slower; the standard library is libwrs.so).  In the check build:
+ *   - every build first zeroes its bucket array, and every bucket store
+ *     adds one to the bucket's reserved word instead of storing 0, so a
+ *     build that wrote each bucket exactly once (Alg. 2 and Alg. 3 assign
+ *     every bucket to one step) leaves 1 in every reserved word, and a
+ *     missed or doubled bucket shows as 0 or 2 in the downloaded table;
+ *   - a bucket index or alias outside the table, a shared-memory index of
+ *     the sweep outside its window, a sweep subproblem that ends in another
+ *     heavy tile than the split search gave the next one (Alg. 3: the state
+ *     at the end of one subproblem is the start of the next), and a sampled
+ *     bucket whose alias lies outside the table each count as a failed
+ *     check: the access is skipped, the table's status becomes
+ *     WRS_EINTERNAL and the count goes to the header's first reserved word.
+ * wrs_check_build: 1 in the check build, 0 in the standard build.
+ * wrs_table_check_failures: wait for the table's last build (as
+ *   wrs_table_status) and store in *failures the failed checks counted
+ *   since that build began (0 in the standard build; failures of a
+ *   sampling are counted once the sampling has completed, so synchronize
+ *   its stream first).  WRS_EINVAL for NULL arguments or a table never
+ *   built. */
+int wrs_check_build(void);
+wrs_status wrs_table_check_failures(const wrs_table *t, uint64_t *failures);
+
 /* Device-side wait limit used by the look-back scan of a build, in polls
  * (default 1 << 22, about a second).  Returns the previous value.  A build
  * whose wait runs out stores WRS_ETIMEOUT in the table's status. */
@@ -466,10 +491,10 @@ wrs_status wrs_table2_sample_os(wrs_table2 *t, const void *d_weights, wrs_dtype 
 #define WRS_NOALLOC_MAX_N (1ull << 22)
 #define WRS_DEVICE_HEADER_BYTES 128
 
-/* Every field is written by every build; the caller only reads them.  The
- * two fields marked "library" are working state of the build: their values
- * after a build carry no meaning for the caller, and the caller must not
- * store into them. */
+/* Every field but reserved2[2..7] is written by every build; the caller
+ * only reads them.  The two fields marked "library" are working state of
+ * the build: their values after a build carry no meaning for the caller,
+ * and the caller must not store into them. */
 typedef struct {
     uint32_t status;      /* wrs_status of the build */
     uint32_t tile_counter; /* library: block ids of the look-back scan */
@@ -481,7 +506,8 @@ typedef struct {
     uint32_t f32;         /* library: 1 if the weights were binary32 words */
     uint64_t n;
     uint64_t n_light;
-    uint64_t reserved2[8];
+    uint64_t reserved2[8]; /* [0], [1]: zero after a build of libwrs.so; the
+                              check build counts failed checks in [0] */
 } wrs_device_header;
 
 wrs_status wrs_build_noalloc(const void *d_weights, uint64_t n, wrs_dtype dtype,

@@ -1,9 +1,11 @@
 """Compile the in-tree CUDA libraries for sm_103a (GB300).
 
 ``libwrs.so``            the product library (C ABI of include/wrs.h)
+``libwrs_check.so``      the same sources with WRS_CHECK=1: bucket write
+                         counts and index checks, for verification
 ``libwrs_workloads.so``  device-side generator of the seeded synthetic inputs
 
-Both are built with nvcc directly into this package directory (no cmake, no
+All are built with nvcc directly into this package directory (no cmake, no
 torch extension machinery) and rebuilt only when a source is newer.
 """
 from __future__ import annotations
@@ -21,10 +23,13 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared"
 
 # libwrs: no multiply-add contraction, so that the OS-ND binomial deviates
 # (binary64 arithmetic) follow the written steps exactly.
-EXTRA = {"libwrs.so": ["-fmad=false"]}
+EXTRA = {"libwrs.so": ["-fmad=false"], "libwrs_check.so": ["-fmad=false", "-DWRS_CHECK=1"]}
 
+_WRS_HEADERS = ["wrs_device.cuh", "wrs_kernels.cuh", "wrs_batch.cuh", "wrs_twolevel.cuh", "wrs_osnd.cuh",
+                "wrs_psaplus.cuh"]
 TARGETS = {
-    "libwrs.so": (["wrs.cu"], ["wrs_device.cuh", "wrs_kernels.cuh", "wrs_batch.cuh", "wrs_twolevel.cuh", "wrs_osnd.cuh", "wrs_psaplus.cuh"], [os.path.join(INCLUDE, "wrs.h")]),
+    "libwrs.so": (["wrs.cu"], _WRS_HEADERS, [os.path.join(INCLUDE, "wrs.h")]),
+    "libwrs_check.so": (["wrs.cu"], _WRS_HEADERS, [os.path.join(INCLUDE, "wrs.h")]),
     "libwrs_workloads.so": (["workloads.cu"], [], []),
 }
 

@@ -100,6 +100,21 @@ inline wrs_status cuda_err(cudaError_t e)
 
 inline wrs_status launch_err() { return cuda_err(cudaGetLastError()); }
 
+// Check build: the buckets start at zero before a build, so that their
+// reserved words count the stores that reach them.  Nothing in the standard
+// build.
+inline wrs_status check_clear(void *buckets, uint64_t count, cudaStream_t s)
+{
+#if WRS_CHECK
+    return cuda_err(cudaMemsetAsync(buckets, 0, count * sizeof(uint4), s));
+#else
+    (void)buckets;
+    (void)count;
+    (void)s;
+    return WRS_OK;
+#endif
+}
+
 int sm_count()
 {
     int dev = 0, sms = 0;
@@ -237,6 +252,10 @@ wrs_status enqueue_build(wrs_table *t, const void *d_weights, uint64_t n, wrs_dt
     const uint32_t nchunks = (ntiles + kScanChunk - 1) / kScanChunk;
     uint32_t cls_blocks = (uint32_t)sm_count() * 8; // one warp per tile
     if (cls_blocks > (ntiles + kWarps - 1) / kWarps) cls_blocks = (ntiles + kWarps - 1) / kWarps;
+    {
+        const wrs_status st = check_clear(t->buckets, n, s);
+        if (st != WRS_OK) return st;
+    }
     const bool tm = t->timing != 0;
     if (tm) cudaEventRecord(t->ev[0], s);
     if (f32) k_stats<1><<<nparts, kThreads, 0, s>>>(w, n, vec, t->part);
@@ -511,6 +530,18 @@ wrs_status wrs_table_info_get(const wrs_table *t, wrs_table_info *info)
     return WRS_OK;
 }
 
+int wrs_check_build(void) { return WRS_CHECK; }
+
+wrs_status wrs_table_check_failures(const wrs_table *t, uint64_t *failures)
+{
+    if (!t || !failures || t->n == 0) return WRS_EINVAL;
+    DevHeader h;
+    const wrs_status st = read_back(t, &h, t->hdr, sizeof(h));
+    if (st != WRS_OK) return st;
+    *failures = h.pad[0];
+    return WRS_OK;
+}
+
 const wrs_bucket *wrs_table_buckets(const wrs_table *t)
 {
     return t ? reinterpret_cast<const wrs_bucket *>(t->buckets) : nullptr;
@@ -746,6 +777,7 @@ extern "C" wrs_status wrs_build_noalloc(const void *d_weights, uint64_t n, wrs_d
     // the look-back flags start from zero on the stream, in stream order with
     // the scan that reads them
     if (cudaMemsetAsync(flags, 0, (size_t)nchunks * sizeof(uint32_t), s) != cudaSuccess) return WRS_EDEVICE;
+    if (check_clear(buckets, n, s) != WRS_OK) return WRS_EDEVICE;
 
     if (f32) k_stats<1><<<nparts, kThreads, 0, s>>>(w, n, vec, part);
     else k_stats<0><<<nparts, kThreads, 0, s>>>(w, n, vec, part);

@@ -123,8 +123,8 @@ __global__ void __launch_bounds__(kThreads, 3) kb_small(const uint32_t *__restri
     block_exclusive_scan_u32(cl, nl, S.cnt);
     if (threadIdx.x == 0) hdr->n_light = nl;
     const bool bad = bitlen128(Q) <= 52
-                         ? group_build<uint64_t>(S, q, Q, (uint32_t)N, N, first, 0, shift, buckets + T.off)
-                         : group_build<u128>(S, q, Q, (uint32_t)N, N, first, 0, shift, buckets + T.off);
+                         ? group_build<uint64_t>(S, q, Q, (uint32_t)N, N, first, 0, shift, buckets + T.off, hdr)
+                         : group_build<u128>(S, q, Q, (uint32_t)N, N, first, 0, shift, buckets + T.off, hdr);
     if (bad) set_status(hdr, kEInternal);
 }
 
@@ -316,6 +316,10 @@ wrs_status batch_enqueue_build(wrs_batch *b, const uint32_t *w, uint32_t f32, cu
                                cudaEvent_t sweep1)
 {
     const int vec = (reinterpret_cast<uintptr_t>(w) % 16) == 0;
+    {
+        const wrs_status st = check_clear(b->buckets, b->total_w, s);
+        if (st != WRS_OK) return st;
+    }
     if (b->nb[kMapSmall]) {
         const size_t gs = sizeof(GroupSmem);
         if (f32) kb_small<1><<<b->nb[kMapSmall], kThreads, gs, s>>>(w, vec, b->d_tables, b->map[kMapSmall], b->hdr, b->buckets);

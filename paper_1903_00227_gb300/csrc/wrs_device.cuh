@@ -38,7 +38,7 @@ struct DevHeader {
     uint32_t f32;
     uint64_t n;
     uint64_t n_light;       // filled by the sweep of the last tile
-    uint64_t pad[2];
+    uint64_t pad[2];        // zero; the check build counts failed checks in pad[0]
 };
 
 struct Partial {            // per-block result of k_stats
@@ -157,6 +157,56 @@ __device__ __forceinline__ void st_release(uint32_t *p, uint32_t v)
 __device__ __forceinline__ void set_status(DevHeader *h, uint32_t code)
 {
     atomicCAS(&h->status, 0u, code);
+}
+
+// ------------------------------------------------------- check build
+// libwrs_check.so is this library compiled with -DWRS_CHECK=1.  There, every
+// bucket store adds one to the bucket's reserved fourth word instead of
+// storing 0 (the build clears the buckets first, so a table in which every
+// bucket was written exactly once has 1 in every reserved word), a bucket
+// index or alias outside the table is refused, and the index checks placed
+// on the sweep's shared-memory reads and on its end-of-subproblem state
+// hold.  A check that fails counts itself in the header's first reserved
+// word, sets WRS_EINTERNAL and skips the access.  In the standard build all
+// of this compiles away and the reserved word is stored as 0.
+#ifndef WRS_CHECK
+#define WRS_CHECK 0
+#endif
+
+__device__ __noinline__ void check_fail(DevHeader *h)
+{
+    atomicAdd(reinterpret_cast<unsigned long long *>(&h->pad[0]), 1ull);
+    set_status(h, kEInternal);
+}
+
+// True when cond holds; in the check build a false cond is recorded.
+__device__ __forceinline__ bool check_ok(bool cond, DevHeader *h)
+{
+    if (WRS_CHECK && !cond) {
+        check_fail(h);
+        return false;
+    }
+    return true;
+}
+
+// Bucket me of a table of `limit` buckets: threshold thr, alias.
+__device__ __forceinline__ void put_bucket(uint4 *table, uint64_t me, uint64_t thr, uint32_t alias, uint64_t limit,
+                                           DevHeader *h)
+{
+#if WRS_CHECK
+    if (me >= limit || alias >= limit) {
+        check_fail(h);
+        return;
+    }
+    uint32_t *p = reinterpret_cast<uint32_t *>(table + me);
+    *reinterpret_cast<uint2 *>(p) = make_uint2((uint32_t)thr, (uint32_t)(thr >> 32));
+    p[2] = alias;
+    atomicAdd(p + 3, 1u);
+#else
+    (void)limit;
+    (void)h;
+    table[me] = make_uint4((uint32_t)thr, (uint32_t)(thr >> 32), alias, 0u);
+#endif
 }
 
 // The table's status, read once for the whole block: every thread returns

@@ -361,6 +361,8 @@ __device__ __forceinline__ uint32_t write_header(const Acc &a, uint64_t n, uint3
     hdr->f32 = f32;
     hdr->n = n;
     hdr->n_light = 0;
+    hdr->pad[0] = 0;
+    hdr->pad[1] = 0;
     __threadfence();
     hdr->status = status;
     return status;
@@ -1024,8 +1026,7 @@ __device__ __forceinline__ void sweep_body(const uint32_t *__restrict__ w, uint6
                     const u128 nq = Q - (dn - S.okey[swz(i)]);
                     if (nq != Q) bad = true;
                     const uint32_t me = (uint32_t)(tile0 + S.ooff[i]);
-                    const uint64_t thr = lo64(nq >> shift);
-                    table[me] = make_uint4((uint32_t)thr, (uint32_t)(thr >> 32), me, 0u);
+                    put_bucket(table, me, lo64(nq >> shift), me, n, hdr);
                 }
                 break;
             }
@@ -1056,6 +1057,9 @@ __device__ __forceinline__ void sweep_body(const uint32_t *__restrict__ w, uint6
             }
             __syncthreads();
             const uint32_t a0 = al, a1 = S.rng[1], b0 = S.rng[2], b1 = S.rng[3];
+            if (WRS_CHECK && !check_ok(hc <= (uint32_t)kTile && nl <= (uint32_t)kTile && a0 <= a1 && a1 <= nl &&
+                                           b0 <= b1 && b1 <= hc, hdr))
+                break;
             const uint32_t na = a1 - a0, nb = b1 > b0 ? b1 - b0 : 0, M = na + nb;
             const uint32_t per = (M + kThreads - 1) / kThreads;
             const uint64_t sbase = (uint64_t)s * kTile;
@@ -1099,6 +1103,7 @@ __device__ __forceinline__ void sweep_body(const uint32_t *__restrict__ w, uint6
                             hp = hp1;
                             hp1 = hpos(j + 1);
                         } else {
+                            if (WRS_CHECK && !check_ok(i < a1, hdr)) break;
                             const u128 dn = (i + 1 < nl) ? S.okey[swz(i + 1)] : D_end;
                             const uint64_t def = lo64(dn) - lo64(di); // < Q: exact modulo 2^64
                             bw = Q64 - def;
@@ -1107,7 +1112,7 @@ __device__ __forceinline__ void sweep_body(const uint32_t *__restrict__ w, uint6
                             ++i;
                             di = dn;
                         }
-                        table[me] = make_uint4((uint32_t)bw, (uint32_t)(bw >> 32), alias, 0u);
+                        put_bucket(table, me, bw, alias, n, hdr);
                     }
                 } else {
                     for (uint32_t st = 0; st < steps; ++st) {
@@ -1126,6 +1131,7 @@ __device__ __forceinline__ void sweep_body(const uint32_t *__restrict__ w, uint6
                             hp = hp1;
                             hp1 = hpos(j + 1);
                         } else { // light i; j < hc: heavy j is its current heavy
+                            if (WRS_CHECK && !check_ok(i < a1, hdr)) break;
                             const u128 dn = (i + 1 < nl) ? S.okey[swz(i + 1)] : D_end;
                             bw = Q - (dn - di);
                             me = (uint32_t)(tile0 + S.ooff[i]);
@@ -1133,13 +1139,17 @@ __device__ __forceinline__ void sweep_body(const uint32_t *__restrict__ w, uint6
                             ++i;
                             di = dn;
                         }
-                        const uint64_t thr = lo64(bw >> shift);
-                        table[me] = make_uint4((uint32_t)thr, (uint32_t)(thr >> 32), alias, 0u);
+                        put_bucket(table, me, lo64(bw >> shift), alias, n, hdr);
                     }
                 }
             }
             al = a1;
-            if (b1 < hc) break; // the first heavy past D_end is in this tile: this own tile is done
+            if (b1 < hc) { // the first heavy past D_end is in this tile: this own tile is done
+                // end of the subproblem: the stream tile carried to the next
+                // own tile is the one k_split found for it independently
+                if (WRS_CHECK && threadIdx.x == 0 && c + 1 < ntiles) check_ok(split[c + 1].hb == s, hdr);
+                break;
+            }
             ++s;
         }
     }
@@ -1186,7 +1196,8 @@ constexpr int kSampleUnroll = 8;
 // Samples first, first + stride, ... (below k) of one table.
 __device__ __forceinline__ void sample_body(const uint4 *__restrict__ tab, uint64_t n, uint64_t qp, uint64_t k,
                                             uint32_t key0, uint32_t key1, uint32_t sid0, uint32_t sid1,
-                                            uint32_t *__restrict__ out, uint64_t first, uint64_t stride)
+                                            uint32_t *__restrict__ out, uint64_t first, uint64_t stride,
+                                            const DevHeader *chk = nullptr)
 {
     for (uint64_t s = first; s < k; s += kSampleUnroll * stride) {
         uint64_t r[kSampleUnroll], v[kSampleUnroll];
@@ -1209,6 +1220,7 @@ __device__ __forceinline__ void sample_body(const uint4 *__restrict__ tab, uint6
             const uint64_t sj = s + j * stride;
             if (sj < k) {
                 const uint64_t thr = b[j].x | ((uint64_t)b[j].y << 32);
+                if (WRS_CHECK && chk) check_ok(b[j].z < n, const_cast<DevHeader *>(chk));
                 const uint32_t pick = (__umul64hi(v[j], qp) < thr) ? (uint32_t)r[j] : b[j].z;
                 __stcs(out + sj, pick);
             }
@@ -1224,7 +1236,7 @@ __global__ void __launch_bounds__(256) k_sample(const uint4 *__restrict__ tab, u
 {
     if (hdr->status) return;
     sample_body(tab, n, hdr->qp, k, key0, key1, sid0, sid1, out,
-                s0 + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, (uint64_t)gridDim.x * blockDim.x);
+                s0 + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, (uint64_t)gridDim.x * blockDim.x, hdr);
 }
 
 } // namespace wrs

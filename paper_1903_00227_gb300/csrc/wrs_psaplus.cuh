@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_pp_local(const uint32_t *__rest
                 const uint32_t nx = (uint32_t)(tile0 + S.hoff[min(j + 1, nh - 1)]);
                 const uint32_t alias = gap == 0 ? me : nx;
                 const uint64_t thr = lo64((Q - gap) >> shift);
-                table[me] = make_uint4((uint32_t)thr, (uint32_t)(thr >> 32), alias, 0u);
+                put_bucket(table, me, thr, alias, n, hdr);
                 ++j;
                 if (j < nh) ej = S.hkey[swz(j)];
             } else { // light i: its own weight, alias the current heavy
@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_pp_local(const uint32_t *__rest
                     else bad = true;
                 }
                 const uint64_t thr = lo64(nq >> shift);
-                table[me] = make_uint4((uint32_t)thr, (uint32_t)(thr >> 32), alias, 0u);
+                put_bucket(table, me, thr, alias, n, hdr);
                 ++i;
                 di = dn;
             }
@@ -479,7 +479,7 @@ __global__ void __launch_bounds__(kThreads) k_pp_merge(const uint4 *__restrict__
                 if (gap > Q || (nx == kNone && gap != 0)) bad = true;
                 const uint32_t alias = (nx == kNone || gap == 0) ? me : nx;
                 const uint64_t thr = lo64((Q - gap) >> shift);
-                table[me] = make_uint4((uint32_t)thr, (uint32_t)(thr >> 32), alias, 0u);
+                put_bucket(table, me, thr, alias, hdr->n, hdr);
                 ++j;
             } else { // light i
                 if (i >= la) { bad = true; break; }
@@ -494,7 +494,7 @@ __global__ void __launch_bounds__(kThreads) k_pp_merge(const uint4 *__restrict__
                     else bad = true;
                 }
                 const uint64_t thr = lo64(v >> shift);
-                table[me] = make_uint4((uint32_t)thr, (uint32_t)(thr >> 32), alias, 0u);
+                put_bucket(table, me, thr, alias, hdr->n, hdr);
                 ++i;
             }
         }
@@ -597,6 +597,8 @@ wrs_status wrs_table_build_psa_plus(wrs_table *t, const void *d_weights, uint64_
     const uint32_t blocks_cap = (uint32_t)sm_count() * 8;
     if (nparts > blocks_cap) nparts = blocks_cap;
 
+    st = check_clear(t->buckets, n, s);
+    if (st != WRS_OK) return st;
     // Q, beta, light_max (the weight-total pass of PSA)
     if (f32) k_stats<1><<<nparts, kThreads, 0, s>>>(w, n, vec, t->part);
     else k_stats<0><<<nparts, kThreads, 0, s>>>(w, n, vec, t->part);

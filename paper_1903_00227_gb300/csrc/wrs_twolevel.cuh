@@ -119,7 +119,7 @@ template <> __device__ __forceinline__ uint64_t thr_of<uint64_t>(uint64_t bw, ui
 template <typename K>
 __device__ __forceinline__ bool group_build(GroupSmem &S, const u128 (&q)[kItems], u128 Qg128, uint32_t ng,
                                             uint64_t N, uint64_t first, uint64_t base, uint32_t shift,
-                                            uint4 *__restrict__ buckets)
+                                            uint4 *__restrict__ buckets, DevHeader *hdr)
 {
     K *okey = reinterpret_cast<K *>(S.okey);
     K *hkey = reinterpret_cast<K *>(S.hkey);
@@ -199,7 +199,7 @@ __device__ __forceinline__ bool group_build(GroupSmem &S, const u128 (&q)[kItems
                 if (nx == kNone && gap != 0) bad = true;
                 const uint32_t alias = (nx == kNone || gap == 0) ? me : nx;
                 const uint64_t thr = thr_of<K>(Qg - gap, shift);
-                buckets[me] = make_uint4((uint32_t)thr, (uint32_t)(thr >> 32), alias, 0u);
+                put_bucket(buckets, me, thr, alias, N, hdr);
                 ++j;
                 if (j < nh) ej = hkey[swzk<K>(j)];
             } else { // light i: its own weight, alias the current heavy (itself when full)
@@ -212,7 +212,7 @@ __device__ __forceinline__ bool group_build(GroupSmem &S, const u128 (&q)[kItems
                     else bad = true;
                 }
                 const uint64_t thr = thr_of<K>(nq, shift);
-                buckets[me] = make_uint4((uint32_t)thr, (uint32_t)(thr >> 32), alias, 0u);
+                put_bucket(buckets, me, thr, alias, N, hdr);
                 ++i;
                 di = dn;
             }
@@ -266,8 +266,8 @@ __global__ void __launch_bounds__(kThreads, 3) k2_group(const void *__restrict__
     }
     // n_g <= 2^11, so every scaled quantity and key is below n_g * Q_g < 2^63
     // when Q_g < 2^52: 64-bit arithmetic is exact (the common case)
-    const bool bad = bits <= 52 ? group_build<uint64_t>(S, q, Qg, ng, N, first, base, shift, buckets)
-                                : group_build<u128>(S, q, Qg, ng, N, first, base, shift, buckets);
+    const bool bad = bits <= 52 ? group_build<uint64_t>(S, q, Qg, ng, N, first, base, shift, buckets, hdr)
+                                : group_build<u128>(S, q, Qg, ng, N, first, base, shift, buckets, hdr);
     if (bad) set_status(hdr, kEInternal);
 }
 
@@ -462,10 +462,14 @@ wrs_status wrs_table2_build(wrs_table2 *t, const void *d_weights, uint64_t n, wr
     uint32_t nparts = (uint32_t)(want < 1 ? 1 : (want > kMaxParts ? kMaxParts : want));
     const uint32_t blocks_cap = (uint32_t)sm_count() * 8;
     if (nparts > blocks_cap) nparts = blocks_cap;
+    const Levels v = levels_for(n);
+    {
+        const wrs_status st = check_clear(t->buckets, levels_buckets(v), s);
+        if (st != WRS_OK) return st;
+    }
     if (f32) k_stats<1><<<nparts, kThreads, 0, s>>>(w, n, vec, t->part);
     else k_stats<0><<<nparts, kThreads, 0, s>>>(w, n, vec, t->part);
     k_stats_combine<<<1, kThreads, 0, s>>>(t->part, nparts, n, f32, t->hdr);
-    const Levels v = levels_for(n);
     const size_t smem = sizeof(GroupSmem);
     for (uint32_t l = 0; l < v.L; ++l) {
         const uint32_t ngroups = (uint32_t)((v.size[l] + kTile - 1) / kTile);

@@ -9,6 +9,10 @@ without the built library raises.
 
 ``AliasTable`` is a small convenience wrapper that owns a table handle and
 takes torch tensors (PyTorch is used only for device memory and streams).
+
+With the environment variable ``WRS_CHECK=1`` set before the first import,
+the binding loads ``libwrs_check.so`` instead: the same entry points
+compiled with bucket write counts and index checks (``wrs_check_build``).
 """
 from __future__ import annotations
 
@@ -16,7 +20,7 @@ import ctypes
 import os
 
 PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(PKG, "libwrs.so")
+LIB_PATH = os.path.join(PKG, "libwrs_check.so" if os.environ.get("WRS_CHECK") == "1" else "libwrs.so")
 
 OK, EINVAL, ENOMEM, EOVERFLOW, ETIMEOUT, EDEVICE, EINTERNAL = range(7)
 U32, F32 = 0, 1
@@ -73,6 +77,8 @@ _sig = {
     "wrs_table_stage_ms": ([_TBL, ctypes.POINTER(ctypes.c_float), ctypes.c_uint32], _I),
     "wrs_table_free": ([_TBL], None),
     "wrs_status_str": ([_I], ctypes.c_char_p),
+    "wrs_check_build": ([], _I),
+    "wrs_table_check_failures": ([_TBL, ctypes.POINTER(ctypes.c_uint64)], _I),
     "wrs_set_wait_limit": ([ctypes.c_uint32], ctypes.c_uint32),
     "wrs_debug_skip_publish": ([ctypes.c_int64], None),
     "wrs_build_noalloc": ([_P, _U64, _I, _P, _P, _P], _I),
@@ -187,6 +193,16 @@ def table_info_get(t):
     info = TableInfo()
     rc = _lib.wrs_table_info_get(t, ctypes.byref(info))
     return rc, info
+
+
+def check_build() -> int:
+    return _lib.wrs_check_build()
+
+
+def table_check_failures(t):
+    m = ctypes.c_uint64(0)
+    rc = _lib.wrs_table_check_failures(t, ctypes.byref(m))
+    return rc, m.value
 
 
 def table_buckets(t) -> int:
@@ -429,6 +445,11 @@ class AliasTable:
         rc, info = table_info_get(self.handle)
         _check(rc, "wrs_table_info_get")
         return info
+
+    def check_failures(self) -> int:
+        rc, m = table_check_failures(self.handle)
+        _check(rc, "wrs_table_check_failures")
+        return m
 
     def download(self):
         import numpy as np

@@ -34,6 +34,19 @@ def test_every_declared_symbol_is_exported(wrs):
     assert sorted(wrs.EXPORTED) == names
 
 
+def test_check_build_exports_the_same_symbols(wrs):
+    """libwrs_check.so (WRS_CHECK=1) has every entry point of the standard
+    library and says which build it is; the standard library says 0."""
+    names = declared_functions()
+    check = ctypes.CDLL(os.path.join(os.path.dirname(wrs.LIB_PATH), "libwrs_check.so"))
+    for name in names:
+        assert hasattr(check, name), name
+    check.wrs_check_build.restype = ctypes.c_int
+    assert check.wrs_check_build() == 1
+    assert wrs.check_build() == (1 if wrs.LIB_PATH.endswith("libwrs_check.so") else 0)
+    assert wrs.table_check_failures(None)[0] == wrs.EINVAL
+
+
 def test_argument_errors_need_no_gpu(wrs):
     rc, h = wrs.table_create(0)
     assert rc == wrs.EINVAL and h is None
