@@ -1032,7 +1032,11 @@ __device__ __forceinline__ void sweep_body(const uint32_t *__restrict__ w, uint6
             }
             if (s != s_loaded) {
                 const uint32_t nheavy = tilesum_ldcg(incl + s).nheavy;
-                if (nheavy == 0) { ++s; continue; }
+                if (nheavy == 0) { // on to the tile of the first heavy after this one
+                    const uint32_t nh = split[s].next_heavy;
+                    s = nh == kNone ? ntiles : nh / (uint32_t)kTile;
+                    continue;
+                }
                 if (y_tile != s && nheavy > (uint32_t)kSparse) {
                     load_items(w, n, vec, (uint64_t)s * kTile + (uint64_t)threadIdx.x * kItems, y);
                     y_tile = s;
@@ -1046,6 +1050,9 @@ __device__ __forceinline__ void sweep_body(const uint32_t *__restrict__ w, uint6
                 }
             }
             const uint32_t hc = S.hcount;
+            // position of the first heavy after stream tile s (kNone: none),
+            // read while the block waits at the barrier
+            const uint32_t hnext = split[s].next_heavy;
             __syncthreads(); // own keys and window complete
             if (threadIdx.x < 3 * 32) { // one warp per search
                 const int q = threadIdx.x >> 5;
@@ -1077,7 +1084,6 @@ __device__ __forceinline__ void sweep_body(const uint32_t *__restrict__ w, uint6
                 u128 di = i < nl ? S.okey[swz(i)] : D_end; // key of light i (D_end past the last)
                 // positions of heavies j and j + 1 (the first heavy after the
                 // stream tile past its last), kept in registers along the walk
-                const uint32_t hnext = split[s].next_heavy;
                 auto hpos = [&](uint32_t jj) -> uint32_t {
                     return jj < hc ? (uint32_t)(sbase + S.hoff[jj]) : hnext;
                 };
@@ -1150,7 +1156,7 @@ __device__ __forceinline__ void sweep_body(const uint32_t *__restrict__ w, uint6
                 if (WRS_CHECK && threadIdx.x == 0 && c + 1 < ntiles) check_ok(split[c + 1].hb == s, hdr);
                 break;
             }
-            ++s;
+            s = hnext == kNone ? ntiles : hnext / (uint32_t)kTile; // the next stream tile with a heavy
         }
     }
     if (bad) set_status(hdr, kEInternal);
