@@ -112,6 +112,8 @@ wrs_status wrs_table_build(wrs_table *t, const void *d_weights, uint64_t n,
  *           library's choice (8 tiles per subproblem); at most the number
  *           of tiles, ceil(n / 2048)
  *   tile    0 or 2048 (the tile is fixed)
+ *   window  0 or 2048: the sweep merges a subproblem's lights with the
+ *           heavy items of one stream tile at a time (its window; fixed)
  *   acc     WRS_ACC_AUTO: 64-bit bucket arithmetic when Q < 2^64, else
  *           128-bit; WRS_ACC_U64: the build fails with WRS_EOVERFLOW (in
  *           the status word) when Q >= 2^64; WRS_ACC_U128: 128-bit
@@ -122,6 +124,7 @@ typedef enum { WRS_ACC_AUTO = 0, WRS_ACC_U64 = 1, WRS_ACC_U128 = 2 } wrs_acc;
 typedef struct {
     uint32_t splits;
     uint32_t tile;
+    uint32_t window;
     uint32_t acc;   /* a wrs_acc */
     uint32_t flags;
 } wrs_build_opts;

@@ -397,6 +397,7 @@ wrs_status wrs_table_build_opts(wrs_table *t, const void *d_weights, uint64_t n,
     if (opts) {
         if (opts->flags != 0) return WRS_EINVAL;
         if (opts->tile != 0 && opts->tile != (uint32_t)kTile) return WRS_EINVAL;
+        if (opts->window != 0 && opts->window != (uint32_t)kTile) return WRS_EINVAL;
         if (opts->acc != WRS_ACC_AUTO && opts->acc != WRS_ACC_U64 && opts->acc != WRS_ACC_U128) return WRS_EINVAL;
         const uint32_t ntiles = (uint32_t)((n + kTile - 1) / kTile);
         if (opts->splits > ntiles) return WRS_EINVAL;

@@ -147,9 +147,9 @@ ACC_AUTO, ACC_U64, ACC_U128 = range(3)
 
 class BuildOpts(ctypes.Structure):
     """wrs_build_opts: split count (0: the library's choice), tile (0 or
-    2048), accumulator mode, flags (0)."""
-    _fields_ = [("splits", ctypes.c_uint32), ("tile", ctypes.c_uint32), ("acc", ctypes.c_uint32),
-                ("flags", ctypes.c_uint32)]
+    2048), window (0 or 2048), accumulator mode, flags (0)."""
+    _fields_ = [("splits", ctypes.c_uint32), ("tile", ctypes.c_uint32), ("window", ctypes.c_uint32),
+                ("acc", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
 
 
 def table_build_opts(t, d_weights: int, n: int, dtype: int, opts: "BuildOpts | None", stream: int = 0) -> int:
@@ -396,12 +396,13 @@ class AliasTable:
         self.n = n
         return self
 
-    def build_opts(self, weights, splits: int = 0, acc: int = 0, tile: int = 0, stream=None) -> "AliasTable":
+    def build_opts(self, weights, splits: int = 0, acc: int = 0, tile: int = 0, window: int = 0,
+                   stream=None) -> "AliasTable":
         """wrs_table_build_opts: the same table for every split count and
         accumulator mode; they choose how the work is cut."""
         _require_cuda(weights, "weights")
         n = weights.numel()
-        o = BuildOpts(splits, tile, acc, 0)
+        o = BuildOpts(splits=splits, tile=tile, window=window, acc=acc, flags=0)
         _check(table_build_opts(self.handle, weights.data_ptr(), n, _dtype_code(weights), o, _stream_handle(stream)),
                "wrs_table_build_opts")
         self.n = n

@@ -53,7 +53,7 @@ def test_argument_errors_need_no_gpu(wrs):
     rc, h = wrs.table_create(1 << 32)
     assert rc == wrs.EINVAL
     assert wrs.table_build(None, 0, 10, wrs.U32, 0) == wrs.EINVAL
-    assert wrs.table_build_opts(None, 0, 10, wrs.U32, wrs.BuildOpts(0, 0, 0, 0), 0) == wrs.EINVAL
+    assert wrs.table_build_opts(None, 0, 10, wrs.U32, wrs.BuildOpts(), 0) == wrs.EINVAL
     assert wrs.table_build_opts(None, 16, 10, wrs.U32, None, 0) == wrs.EINVAL
     assert wrs.sample(None, 10, 1, 0, 0, 0) == wrs.EINVAL
     assert wrs.table_status(None) == wrs.EINVAL

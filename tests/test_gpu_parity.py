@@ -282,7 +282,8 @@ def test_build_options_do_not_change_the_table():
         with wrs.AliasTable(len(w)) as t:
             for splits in sorted({0, 1, 2, 3, 64, ntiles} & set(range(ntiles + 1))):
                 for acc in (wrs.ACC_AUTO, wrs.ACC_U128):
-                    t.build_opts(w_dev, splits=splits, acc=acc)
+                    t.build_opts(w_dev, splits=splits, acc=acc, tile=2048 if splits == 1 else 0,
+                                 window=2048 if splits == 2 else 0)
                     assert t.status() == wrs.OK, (splits, acc)
                     thr, alias, _ = t.download()
                     assert np.array_equal(thr, tab.thr) and np.array_equal(alias, tab.alias), (len(w), splits, acc)
@@ -293,6 +294,6 @@ def test_build_options_do_not_change_the_table():
             assert np.array_equal(got, O.sample(tab.thr, tab.alias, tab.Qp, 5000, 3, 0))
     with wrs.AliasTable(10) as t:
         w_dev = G.to_device(np.ones(10, np.uint32))
-        for bad in (wrs.BuildOpts(2, 0, 0, 0), wrs.BuildOpts(0, 1024, 0, 0), wrs.BuildOpts(0, 0, 3, 0),
-                    wrs.BuildOpts(0, 0, 0, 1)):
+        for bad in (wrs.BuildOpts(splits=2), wrs.BuildOpts(tile=1024), wrs.BuildOpts(window=4096),
+                    wrs.BuildOpts(acc=3), wrs.BuildOpts(flags=1)):
             assert wrs.table_build_opts(t.handle, w_dev.data_ptr(), 10, wrs.U32, bad, 0) == wrs.EINVAL
