@@ -283,13 +283,14 @@ __global__ void __launch_bounds__(256) k2_sample(const uint4 *__restrict__ bucke
     if (hdr->status) return;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t s = s0 + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < k; s += kSample2Unroll * stride) {
-        uint64_t g[kSample2Unroll];
+        uint32_t g[kSample2Unroll]; // indices below 2^32 (n < 2^32): 32-bit state, more blocks per SM
 #pragma unroll
         for (int j = 0; j < kSample2Unroll; ++j) g[j] = 0;
 #pragma unroll
         for (int d = 0; d < kMaxLevels; ++d) {
             if (d >= (int)lv.L) break;
-            uint64_t r[kSample2Unroll], v[kSample2Unroll], qp[kSample2Unroll], b0[kSample2Unroll];
+            uint64_t v[kSample2Unroll], qp[kSample2Unroll];
+            uint32_t r[kSample2Unroll], b0[kSample2Unroll];
             uint4 bk[kSample2Unroll];
 #pragma unroll
             for (int j = 0; j < kSample2Unroll; ++j) {
@@ -299,14 +300,14 @@ __global__ void __launch_bounds__(256) k2_sample(const uint4 *__restrict__ bucke
                 const P4 o = philox4x32_10(c, key0 + (uint32_t)d * 0x9E3779B9u, key1 + (uint32_t)d * 0xBB67AE85u);
                 const uint64_t u = o.x0 | ((uint64_t)o.x1 << 32);
                 v[j] = o.x2 | ((uint64_t)o.x3 << 32);
-                b0[j] = g[j] * kTile;
+                b0[j] = g[j] * (uint32_t)kTile;
                 const uint64_t ngj = min((uint64_t)kTile, lv.size[d] - b0[j]);
-                r[j] = __umul64hi(u, ngj);
+                r[j] = (uint32_t)__umul64hi(u, ngj);
             }
 #pragma unroll
             for (int j = 0; j < kSample2Unroll; ++j) {
                 if (s + j * stride < k) {
-                    bk[j] = ld_bucket(buckets + lv.off[d] + b0[j] + r[j]);
+                    bk[j] = ld_bucket(buckets + lv.off[d] + (uint64_t)(b0[j] + r[j]));
                     qp[j] = __ldg(&groups[lv.goff[d] + g[j]].qp);
                 }
             }
