@@ -882,6 +882,11 @@ __device__ __forceinline__ uint32_t warp_search(const u128 *key, uint32_t lo, ui
     return lo + (uint32_t)__popc(__ballot_sync(0xFFFFFFFFu, before));
 }
 
+// Heavies of a stream tile up to which load_heavies compacts their words
+// first: the keys of heavies 0 .. c-1 end below byte 16 (c + 8) of the key
+// array, and the words sit in its top 4 c bytes (16 (c + 8) <= 32768 - 4 c).
+constexpr uint32_t kCompactMax = 1600;
+
 // Keys of stream tile t's heavies into S.hkey/S.hoff (all threads call).
 template <int F32>
 __device__ __forceinline__ void load_heavies(SweepSmem &S, uint32_t t, const uint32_t (&y)[kItems], uint32_t nheavy,
@@ -920,6 +925,43 @@ __device__ __forceinline__ void load_heavies(SweepSmem &S, uint32_t t, const uin
         if (first + k < n && y[k] > light_max) hm |= 1u << k;
     uint32_t ctot;
     const uint32_t slot0 = block_exclusive_scan_u32((uint32_t)__popc(hm), ctot, S.cnt);
+    if (ctot <= kCompactMax) {
+        // Compacted first: the heavies' words go, in index order, to the top
+        // of the key array (below it the keys of the first ctot heavies
+        // never reach them), then thread t keys heavies [t q, t q + q),
+        // q = ceil(ctot / 256): every lane runs the same number of steps
+        // whatever the share of heavies in its eight words.
+        uint32_t *raw = reinterpret_cast<uint32_t *>(S.hkey) + (kTile * 4 - ctot);
+        {
+            uint32_t slot = slot0;
+#pragma unroll
+            for (int k = 0; k < kItems; ++k) {
+                if ((hm >> k) & 1u) {
+                    raw[slot] = y[k];
+                    S.hoff[slot] = (uint16_t)(threadIdx.x * kItems + k);
+                    ++slot;
+                }
+            }
+        }
+        __syncthreads();
+        const uint32_t q = (ctot + kThreads - 1) / kThreads;
+        const uint32_t j0 = min(threadIdx.x * q, ctot), j1 = min(j0 + q, ctot);
+        u128 sum = 0;
+        for (uint32_t j = j0; j < j1; ++j) {
+            const u128 e = nq_of(raw[j], F32, beta, n32) - Q;
+            S.hkey[swz(j)] = e;
+            sum += e;
+        }
+        u128 tot;
+        u128 key = base + block_exclusive_scan1(sum, tot, S.scan);
+        for (uint32_t j = j0; j < j1; ++j) {
+            key += S.hkey[swz(j)];
+            S.hkey[swz(j)] = key;
+        }
+        if (threadIdx.x == 0) S.hcount = ctot;
+        __syncthreads();
+        return;
+    }
     // excesses n*q - Q into the key slots, then an in-place prefix
     u128 sum = 0;
     {
